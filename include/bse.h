@@ -1,0 +1,213 @@
+/*
+ * bse.h -- C ABI of the GB300 (sm_103a) iterative Bethe-Salpeter eigensolver.
+ *
+ * The library computes the lowest excitation eigenpairs of the dense BSE
+ * problem in both forms treated by the paper:
+ *
+ *   Tamm-Dancoff (TDA): A x = lambda x, A Hermitian N x N
+ *       (the C = 0 case, Sec. 1 after Eq. 3);
+ *   pseudo-Hermitian (PH): H z = omega z with
+ *       H = [[A, B], [-conj(B), -conj(A)]]  (Eq. 1, optical case of Sec. 1:
+ *       R = A Hermitian, C = B complex symmetric, anti-resonant block conj(A)),
+ *       right eigenvectors z = (X; Y) normalised to z^H Omega z = 1 with
+ *       Omega = diag(I, -I) (Eq. 2).
+ *
+ * The PH solve is a structure-preserving thick-restart Lanczos on the folded
+ * operator (Sec. 2.2.1): it never forms the 2N x 2N matrix and works only with
+ * the stored blocks A and B.  Every arithmetic step runs in CUDA kernels of
+ * this library; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *   - Complex matrices are interleaved (re, im) pairs, row-major, full N x N
+ *     storage.  Only the upper triangle (i <= j) of A and B is read: A is taken
+ *     as Hermitian (its diagonal's imaginary part is ignored) and B as
+ *     symmetric.
+ *   - Vectors and blocks of vectors are column-major with leading dimension N
+ *     (TDA) or 2N (stacked PH vectors (X; Y)), complex, in the handle's dtype.
+ *   - Every function returns a bse_status; no exception or abort crosses the
+ *     ABI.  On an error the handle stays valid unless stated otherwise.
+ *   - All device work of one handle runs on the CUDA stream given at creation;
+ *     functions that return host data synchronise that stream.  A handle must
+ *     not be used from two threads at once.
+ */
+#ifndef BSE_H_
+#define BSE_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bse_handle bse_handle;
+
+typedef enum bse_status {
+  BSE_OK = 0,
+  BSE_EINVAL = 1,     /* invalid argument (size, pointer, enum, nev > N, ...)  */
+  BSE_ENOMEM = 2,     /* device or host allocation failed                       */
+  BSE_ENOTPD = 3,     /* M of Eq. 2 not positive definite (negative K-norm or   */
+                      /* non-positive Ritz value omega^2 met by the iteration)  */
+  BSE_ENOCONV = 4,    /* fewer than nev pairs converged within maxit steps;     */
+                      /* the converged ones are still returned                  */
+  BSE_ETIMEOUT = 5,   /* a device-side iteration limit expired                  */
+  BSE_ECUDA = 6,      /* a CUDA runtime call failed                             */
+  BSE_ESTATE = 7,     /* call out of order (e.g. backward before a solve)       */
+  BSE_ENOTFINITE = 8  /* NaN or Inf met in the Lanczos coefficients             */
+} bse_status;
+
+typedef enum bse_form { BSE_TDA = 0, BSE_PH = 1 } bse_form;
+
+typedef enum bse_dtype {
+  /* complex64 storage of A, B and of the Krylov basis; FP32 products;
+     FP64 projected eigenproblem, Ritz coefficients, final residuals and
+     Rayleigh-quotient refinement (the mixed-precision path) */
+  BSE_C64 = 0,
+  /* complex128 storage; FP64 products (the FP64 path) */
+  BSE_C128 = 1,
+  /* alias of BSE_C64, kept for the survey's naming of the mixed path */
+  BSE_C64_MIXED = 2
+} bse_dtype;
+
+typedef enum bse_where { BSE_HOST = 0, BSE_DEVICE = 1 } bse_where;
+
+typedef enum bse_which { BSE_LOWEST = 0 } bse_which;
+
+/* Operators for bse_apply (all ignore the lower triangles of A and B). */
+typedef enum bse_op {
+  BSE_OP_A = 0,       /* Y = A X                                  (N rows)  */
+  BSE_OP_MPLUS = 1,   /* Y = A X + B conj(X)   (real-linear half) (N rows)  */
+  BSE_OP_MMINUS = 2,  /* Y = A X - B conj(X)                      (N rows)  */
+  BSE_OP_H = 3        /* Y = H X, X and Y stacked (X1; X2), 2N rows         */
+} bse_op;
+
+/* Solver options.  Zero-initialise and set what you need; zero fields take
+   the defaults given in brackets. */
+typedef struct bse_solve_opts {
+  int ncv;            /* Krylov subspace size m [max(2 nev, nev + 32), <= N] */
+  int maxit;          /* limit on Krylov steps [20000]                        */
+  uint64_t seed;      /* start vector seed [12345]                            */
+  const void* v0;     /* optional device start vector (N complex, handle
+                         dtype); NULL = counter-based random start            */
+  double lock_tol;    /* Ritz-estimate tolerance used for locking, relative
+                         to the Ritz value [tol / 4]                          */
+} bse_solve_opts;
+
+/* Per-solve counters, filled by bse_get_stats after a solve. */
+typedef struct bse_stats {
+  int64_t steps;         /* Krylov steps (one new basis vector each)          */
+  int64_t passes;        /* structured products over the stored A (and B)     */
+  int64_t restarts;      /* thick restarts                                    */
+  int nconv;             /* converged eigenpairs                              */
+  double max_residual;   /* max FP64 relative residual of returned pairs      */
+  double ms_total;       /* device time of the last solve (CUDA events)       */
+  double ms_product;     /* device time inside the structured products        */
+} bse_stats;
+
+/* Human-readable message for a status code (static storage). */
+const char* bse_strerror(int status);
+
+/*
+ * bse_create -- copy and repack A (and B) into the library's device storage.
+ *
+ *   N       order of A and B, 1 <= N <= 2^31 - 1
+ *   A, B    full N x N row-major complex matrices in the precision of dtype
+ *           (complex64 for BSE_C64/BSE_C64_MIXED, complex128 for BSE_C128),
+ *           on the host or the device as `where` says.  B is ignored for
+ *           BSE_TDA and may be NULL there; it is required for BSE_PH.
+ *   form    BSE_TDA or BSE_PH
+ *   stream  cudaStream_t (NULL = legacy default stream)
+ *   out     receives the handle
+ *
+ * Ownership: the library copies A and B into packed upper-triangle tiles in
+ * its own device memory (about N^2 * elem_size bytes for A and B together);
+ * the caller may free its buffers as soon as the call returns.  The handle
+ * owns all its device memory and releases it in bse_destroy.
+ * Paper: the redistribution of Sec. 2.1.2 / 2.2.2 from the application's
+ * layout into the solver's layout, here onto one GPU.
+ */
+int bse_create(int64_t N, const void* A, const void* B, int form, int dtype,
+               int where, void* stream, bse_handle** out);
+
+/*
+ * bse_create_batched -- one handle for `count` independent problems of
+ * uneven orders N[i] (same form and dtype), solved together by
+ * bse_solve_batched in lock-step launches.  A[i], B[i] as in bse_create.
+ */
+int bse_create_batched(int count, const int64_t* N, const void* const* A,
+                       const void* const* B, int form, int dtype, int where,
+                       void* stream, bse_handle** out);
+
+/*
+ * bse_solve -- lowest `nev` eigenpairs (BSE_LOWEST: smallest positive omega
+ * for PH, smallest lambda for TDA, ascending).
+ *
+ *   tol        relative residual target ||H z - omega z|| <= tol |omega| ||z||
+ *              (TDA: ||A x - lambda x|| <= tol |lambda| ||x||), e.g. 1e-12
+ *              for BSE_C128 and 1e-6 for BSE_C64
+ *   eval_out   host array of nev doubles (eigenvalues, FP64 Rayleigh
+ *              quotients of the returned vectors)
+ *   evec_out   device array or NULL: TDA N x nev, PH 2N x nev (stacked
+ *              (X; Y), Omega-normalised), column-major, handle dtype
+ *   nconv_out  host int or NULL: number of converged pairs
+ *
+ * The eigenvectors stay in the handle for bse_backward.  Method: the
+ * structure-preserving thick-restart Lanczos of Sec. 2.2.1 (spectrum folding
+ * for PH), eigenvector recovery and the partner relations of Eq. 7.
+ * Returns BSE_ENOCONV (with *nconv_out < nev) if maxit is reached.
+ */
+int bse_solve(bse_handle* h, int nev, double tol, int which, double* eval_out,
+              void* evec_out, int* nconv_out);
+
+/* bse_solve with options (opts may be NULL). */
+int bse_solve_ex(bse_handle* h, int nev, double tol, int which,
+                 const bse_solve_opts* opts, double* eval_out, void* evec_out,
+                 int* nconv_out);
+
+/*
+ * bse_solve_batched -- solve every problem of a batched handle.
+ *   eval_out   host, count * nev doubles (problem-major)
+ *   evec_out   host array of `count` device pointers (each as in bse_solve)
+ *              or NULL
+ *   nconv_out  host, count ints, or NULL
+ */
+int bse_solve_batched(bse_handle* h, int nev, double tol, int which,
+                      const bse_solve_opts* opts, double* eval_out,
+                      void* const* evec_out, int* nconv_out);
+
+/*
+ * bse_backward -- Hellmann-Feynman adjoint of the last solve.
+ *
+ * Given g = dL/dlambda (nev doubles, host or device as `where` says),
+ * writes the full N x N gradients (row-major, handle dtype, device memory):
+ *   TDA: dA = X diag(g) X^H
+ *   PH : dA = X diag(g) X^H + conj(Y diag(g) Y^H)      (Hermitian)
+ *        dB = X diag(g) Y^H + (X diag(g) Y^H)^T         (symmetric)
+ * from d omega = z^H Omega dH z with the left eigenvector Omega z (Eq. 7).
+ * Convention (PyTorch's): dL = Re<dA, E_A> + Re<dB, E_B> for Hermitian E_A
+ * and symmetric E_B, <G, E> = sum conj(G_ij) E_ij.  dB must be NULL for TDA.
+ * Degenerate eigenvalues need a loss symmetric over each degenerate group.
+ * Returns BSE_ESTATE if no solve has completed on h.
+ */
+int bse_backward(bse_handle* h, const double* dL_dlambda, int where, void* dA,
+                 void* dB);
+
+/*
+ * bse_apply -- one structured product on device blocks of k columns.
+ *   X, Y   device, column-major, handle dtype; N rows (BSE_OP_A/MPLUS/MMINUS)
+ *          or 2N rows (BSE_OP_H); X and Y must not overlap.
+ * Each stored tile of A and B is read once per call and serves both block
+ * rows (A = A^H, B = B^T).  Only for single-problem handles.
+ */
+int bse_apply(bse_handle* h, int op, int k, const void* X, void* Y);
+
+/* Counters of the last solve (single-problem handles; for batched handles
+   the sums over problems). */
+int bse_get_stats(const bse_handle* h, bse_stats* out);
+
+/* Release every resource of the handle (synchronises its stream). */
+int bse_destroy(bse_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSE_H_ */

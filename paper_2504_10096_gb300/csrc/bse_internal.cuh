@@ -1,0 +1,188 @@
+// Internal declarations shared by the translation units of libbse.
+//
+// Storage layout in HBM (one problem):
+//   * A and B as packed upper-triangle tiles of TS x TS complex elements,
+//     tile (I, J), I <= J, in row-major order over the triangle, each tile
+//     row-major; diagonal tiles hold both halves (Hermitian / symmetric
+//     completion); rows and columns beyond N are zero.
+//   * vectors as Npad = nT * TS complex entries (zero padded); blocks of
+//     vectors column-major with leading dimension Npad.
+//   * the Lanczos basis V and its image P = M+ V (PH) as Npad x NCOL, with
+//     columns [0, ncv] the Krylov basis and [ncv+1, ncv+1+ncv) the "twins"
+//     i M+ y / omega of the kept Ritz vectors y.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bse {
+
+constexpr int TS = 128;            // tile edge of the packed storage
+constexpr int PROD_THREADS = 256;  // 16 x 16 threads per tile
+constexpr int ROWBLK = 2048;       // rows per CTA in the tall-skinny reductions
+constexpr int MAXM = 1024;         // largest Krylov subspace supported
+
+// ---------------------------------------------------------------- complex
+template <typename R> struct C2;
+template <> struct C2<float> { using T = float2; };
+template <> struct C2<double> { using T = double2; };
+
+__host__ __device__ inline double2 mk(double x, double y) { return make_double2(x, y); }
+__host__ __device__ inline float2 mk(float x, float y) { return make_float2(x, y); }
+
+template <typename T> __host__ __device__ inline T czero();
+template <> __host__ __device__ inline float2 czero<float2>() { return make_float2(0.f, 0.f); }
+template <> __host__ __device__ inline double2 czero<double2>() { return make_double2(0.0, 0.0); }
+
+// y += a * x
+__host__ __device__ inline void cfma(double2& y, double2 a, double2 x) {
+  y.x = fma(a.x, x.x, y.x); y.x = fma(-a.y, x.y, y.x);
+  y.y = fma(a.x, x.y, y.y); y.y = fma(a.y, x.x, y.y);
+}
+__host__ __device__ inline void cfma(float2& y, float2 a, float2 x) {
+  y.x = fmaf(a.x, x.x, y.x); y.x = fmaf(-a.y, x.y, y.x);
+  y.y = fmaf(a.x, x.y, y.y); y.y = fmaf(a.y, x.x, y.y);
+}
+// y += conj(a) * x
+__host__ __device__ inline void cfmac(double2& y, double2 a, double2 x) {
+  y.x = fma(a.x, x.x, y.x); y.x = fma(a.y, x.y, y.x);
+  y.y = fma(a.x, x.y, y.y); y.y = fma(-a.y, x.x, y.y);
+}
+__host__ __device__ inline void cfmac(float2& y, float2 a, float2 x) {
+  y.x = fmaf(a.x, x.x, y.x); y.x = fmaf(a.y, x.y, y.x);
+  y.y = fmaf(a.x, x.y, y.y); y.y = fmaf(-a.y, x.x, y.y);
+}
+template <typename T> __host__ __device__ inline T conjc(T a) { a.y = -a.y; return a; }
+template <typename T> __host__ __device__ inline T cadd(T a, T b) { a.x += b.x; a.y += b.y; return a; }
+template <typename T> __host__ __device__ inline T csub(T a, T b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename T, typename R> __host__ __device__ inline T cscale(T a, R s) { a.x *= s; a.y *= s; return a; }
+
+struct alignas(32) D4 { double x, y, z, w; };
+
+template <typename To, typename From> __host__ __device__ inline To ccvt(From a) {
+  To r; r.x = a.x; r.y = a.y; return r;
+}
+
+// ---------------------------------------------------------------- state
+enum Status : int {
+  ST_OK = 0, ST_NOTPD = 3, ST_NOCONV = 4, ST_TIMEOUT = 5, ST_NOTFINITE = 8,
+};
+
+// Dynamic Krylov state of one problem, device resident.
+struct KState {
+  int k;        // locked Ritz vectors: columns [0, k)
+  int l;        // kept (locked + arrow) vectors: columns [0, l)
+  int j;        // index of the newest basis vector
+  int m;        // ncv
+  int ntw;      // twins in use
+  int nev;
+  int status;   // Status
+  int done;     // 1 when k >= nev (or stopped)
+  int breakdown;
+  // pending restart decision (written by k_lock_decide, consumed by restart kernels)
+  int r_k0, r_nl, r_nkeep, r_pkeep;
+  long long steps, passes, restarts, maxit;
+  double tol, lock_tol;
+  double beta_last;   // beta_{m-1}: coupling of the last vector to V[:, m]
+};
+
+// Static description of one problem (device resident, read-only in kernels).
+struct Prob {
+  int64_t N;
+  int nT;
+  int64_t Npad;       // nT * TS
+  int ph;             // 1 for the pseudo-Hermitian form
+  int ncv;
+  int ncol;           // columns of V / P: ncv + 1 + ncv
+  const void* A;      // packed tiles
+  const void* B;      // packed tiles (PH) or null
+  void* V;            // Npad x ncol
+  void* P;            // Npad x ncol (PH)
+  void* V2;           // Npad x ncv restart scratch
+  void* P2;
+  void* w;            // Npad work vectors
+  void* pw;
+  void* part;         // product partials nT * nT * TS * KMAXP (compute type)
+  double* cpart;      // CGS / norm partials: nrb * ncol complex
+  double* coef;       // 2 * ncol complex (pass 1, pass 2)
+  double* theta;      // [ncv + 1] Ritz values of kept vectors
+  double* barrow;     // [ncv + 1] arrow couplings
+  double* alpha;      // [ncv + 1]
+  double* beta;       // [ncv + 1] beta[t] couples t and t+1
+  double* ritz;       // [ncv] Ritz values of the active block
+  double* rest;       // [ncv] Ritz estimates
+  double* S;          // ncv x ncv, column-major, ld ncv
+  int nrb;            // row blocks of the tall-skinny reductions
+  KState* st;
+};
+
+// Jobs of the tiled product: problem, tile row I, tile column J, tile index.
+struct TileJob { int prob, I, J, t; };
+
+// Product modes (which vectors feed the product and where the result goes).
+enum ProdMode : int {
+  PM_STEP_MMINUS = 0,  // w  = A p_j - B conj(p_j)    (PH step, first pass)
+  PM_STEP_MPLUS = 1,   // pw = A w + B conj(w)         (PH step, second pass)
+  PM_STEP_A = 2,       // w  = A v_j                   (TDA step)
+  PM_START_MPLUS = 3,  // pw = A w + B conj(w) at start / new-vector time
+  PM_GENERIC = 4,      // Y = A XA + sB B XB, explicit blocks (K columns)
+};
+
+struct GenericIO {     // explicit operands for PM_GENERIC (single problem)
+  const void* xa; const void* xb;  // Npad x K blocks (compute type) ; xb may be null -> conj(xa)
+  int ldx;
+  double sB;           // sign of the B term (0 disables it)
+  void* y; int ldy;    // output (compute type) Npad x K
+};
+
+// ---------------------------------------------------------------- launchers
+// packing (k_product.cu): tiles (I, J >= I) of block row I from TS rows
+template <typename TIn, typename TSt>
+void launch_pack_row(const TIn* rows, int64_t N, int nT, int I, int herm, TSt* dst, cudaStream_t s);
+
+// products (k_product.cu); ST = storage complex type, R = compute real type
+template <typename ST, typename R>
+void launch_product(const Prob* dprobs, const TileJob* jobs, int njobs, int nprob, int maxnT,
+                    int mode, int K, const GenericIO* io_host, bool hasB, cudaStream_t s);
+template <typename ST, typename R>
+void launch_rowblock(const Prob* dprobs, int prob, int nT, const void* xa, const void* xb, int ldx,
+                     double sB, void* y, int ldy, int K, bool hasB, cudaStream_t s);
+
+// Krylov kernels (k_krylov.cu)
+template <typename ST>
+void launch_step_cgs(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t maxNpad,
+                     int ncol, int pass, cudaStream_t s);
+template <typename ST>
+void launch_step_normalize(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t maxNpad,
+                           int start, cudaStream_t s);
+template <typename ST>
+void launch_start_vector(const Prob* dprobs, int nprob, int64_t maxNpad, uint64_t seed,
+                         const void* v0, cudaStream_t s);
+template <typename ST>
+void launch_restart(const Prob* dprobs, int nprob, int ph, int64_t maxNpad, int ncv,
+                    cudaStream_t s);
+
+// projected eigenproblem (k_ritz.cu)
+void launch_ritz(const Prob* dprobs, int nprob, int ncv, cudaStream_t s);
+void launch_lock_decide_form(const Prob* dprobs, int nprob, int ph, cudaStream_t s);
+
+// post-processing (k_post.cu); Z is FP64, ld 2 Npad (PH) or Npad (TDA)
+template <typename ST>
+void launch_recover(const Prob* dprobs, int iprob, int ph, int64_t Npad, int64_t N, int nev,
+                    double2* Z, int ldz, cudaStream_t s);
+void launch_colnormalize(double2* Z, int64_t ldz, int64_t Npad, int k, int ph, double* part,
+                         int nrb, cudaStream_t s);
+void launch_prepare_hz2(const double2* Z, int64_t ldz, int64_t Npad, int k, double2* XA,
+                        double2* XB, cudaStream_t s);
+void launch_residuals2(const double2* Z, int64_t ldz, const double2* U, int64_t Npad, int k,
+                       int ph, D4* part, int nrb, double* rho, double* znorm2, double* res,
+                       cudaStream_t s);
+template <typename ST>
+void launch_store_vectors2(const double2* Z, int64_t ldz, int64_t Npad, int64_t N, int ph, int k,
+                           const int* perm, ST* out, int64_t ldo, cudaStream_t s);
+template <typename ST, typename R>
+void launch_adjoint2(const double2* Z, int64_t ldz, int64_t Npad, int64_t N, int k,
+                     const double* g, int ph, const int2* tiles, int64_t ntiles, ST* dA, ST* dB,
+                     cudaStream_t s);
+
+}  // namespace bse

@@ -1,0 +1,449 @@
+// Krylov-basis kernels of the thick-restart Lanczos iteration.
+//
+// Inner product: TDA uses the Euclidean one; the pseudo-Hermitian (folded)
+// iteration uses <x, y>_K = Re(x^H M+ y) on C^N viewed as R^2N, in which the
+// folded operator T = M- M+ (eigenvalues omega^2, Sec. 2.2.1) is self-adjoint.
+// P = M+ V is stored next to V, so every K-inner product against the basis is
+// Re(P^H w): one pass over the stored blocks per Krylov step is spent on
+// M- p_j, the other on M+ w for the norm (the "two passes" of the step).
+//
+// Re-orthogonalisation is classical Gram-Schmidt done twice (CGS2) against
+// the whole basis, including the "twins" i M+ y / omega of the kept Ritz
+// vectors y.  The folded operator has every omega^2 twice (y and its twin),
+// and rounding noise along the twins would otherwise be amplified into
+// duplicate Ritz values; in exact arithmetic the twins are K-orthogonal to
+// the Krylov space, so removing those components changes nothing else.
+#include "bse_internal.cuh"
+
+namespace bse {
+
+template <typename ST> struct RealOf;
+template <> struct RealOf<float2> { using T = float; };
+template <> struct RealOf<double2> { using T = double; };
+
+__device__ __forceinline__ bool kactive(const KState* st) {
+  return !st->done && st->status == ST_OK && !st->breakdown && st->j < st->m;
+}
+// problems that need a fresh basis vector: the very first one (j < 0) or a
+// replacement after an invariant subspace was found (breakdown)
+__device__ __forceinline__ bool kfresh(const KState* st) {
+  return !st->done && st->status == ST_OK && (st->j < 0 || st->breakdown);
+}
+__device__ __forceinline__ bool kphase(const KState* st, int fresh) {
+  return fresh ? kfresh(st) : kactive(st);
+}
+
+// column index of basis entry c of the orthogonalisation set [0..j] U twins
+__device__ __forceinline__ int set_col(int c, int j, int ncv) {
+  return c <= j ? c : (ncv + 1) + (c - (j + 1));
+}
+
+__device__ __forceinline__ double2 dshfl(double2 v, int m) {
+  v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+  v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+  return v;
+}
+
+// ---------------------------------------------------------------- CGS2 dots
+// cpart[rb][c] = sum_{rows in block rb} conj(Q[row, col(c)]) w[row],
+// Q = P (PH) or V (TDA).  grid (ceil(maxcols/8), maxnrb, nprob), 8 warps.
+template <typename ST>
+__global__ void __launch_bounds__(256)
+k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec) {
+  using R = typename RealOf<ST>::T;
+  const Prob& p = probs[blockIdx.z];
+  const KState* st = p.st;
+  if (!kphase(st, newvec)) return;
+  const int rb = blockIdx.y;
+  if (rb >= p.nrb) return;
+  const int j = st->j;
+  const int nset = (j + 1) + (ph ? st->ntw : 0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 8 + warp;
+  if (c >= nset) return;
+  const int col = set_col(c, j, p.ncv);
+  const ST* Q = (const ST*)(ph ? p.P : p.V) + (int64_t)col * p.Npad;
+  const ST* w = (const ST*)p.w;
+  const int64_t r0 = (int64_t)rb * ROWBLK;
+  const int64_t r1 = min((int64_t)p.Npad, r0 + ROWBLK);
+  ST acc = czero<ST>();
+  for (int64_t r = r0 + lane; r < r1; r += 32) cfmac(acc, __ldg(Q + r), __ldg(w + r));
+  double2 a = mk((double)acc.x, (double)acc.y);
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) a = cadd(a, dshfl(a, m));
+  if (lane == 0) ((double2*)p.cpart)[(int64_t)rb * p.ncol + c] = a;
+}
+
+// coef[pass][c] = sum_rb cpart[rb][c] (PH: real part only).
+__global__ void k_cgs_coef(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
+  const Prob& p = probs[blockIdx.y];
+  const KState* st = p.st;
+  if (!kphase(st, newvec)) return;
+  const int j = st->j;
+  const int nset = (j + 1) + (ph ? st->ntw : 0);
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nset) return;
+  const double2* cp = (const double2*)p.cpart;
+  double2 s = mk(0.0, 0.0);
+  for (int rb = 0; rb < p.nrb; ++rb) s = cadd(s, cp[(int64_t)rb * p.ncol + c]);
+  if (ph) s.y = 0.0;
+  ((double2*)p.coef)[(int64_t)pass * p.ncol + c] = s;
+}
+
+// w[row] -= sum_c V[row, col(c)] coef[pass][c].  grid (ceil(maxNpad/128), nprob).
+template <typename ST>
+__global__ void __launch_bounds__(128)
+k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
+  using R = typename RealOf<ST>::T;
+  __shared__ ST cf[2 * MAXM + 1];
+  const Prob& p = probs[blockIdx.y];
+  const KState* st = p.st;
+  if (!kphase(st, newvec)) return;
+  const int j = st->j;
+  const int nset = (j + 1) + (ph ? st->ntw : 0);
+  const double2* coef = (const double2*)p.coef + (int64_t)pass * p.ncol;
+  for (int c = threadIdx.x; c < nset; c += blockDim.x) cf[c] = ccvt<ST>(coef[c]);
+  __syncthreads();
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= p.Npad) return;
+  const ST* V = (const ST*)p.V;
+  ST acc = czero<ST>();
+  if (ph) {
+    for (int c = 0; c < nset; ++c) {
+      const ST v = __ldg(V + (int64_t)set_col(c, j, p.ncv) * p.Npad + row);
+      const R f = cf[c].x;
+      acc.x = fma(v.x, f, acc.x);
+      acc.y = fma(v.y, f, acc.y);
+    }
+  } else {
+    for (int c = 0; c < nset; ++c) cfma(acc, __ldg(V + (int64_t)c * p.Npad + row), cf[c]);
+  }
+  ST* w = (ST*)p.w;
+  w[row] = csub(w[row], acc);
+}
+
+// ---------------------------------------------------------------- norms
+// cpart[rb].x = sum over rows of Re(conj(w) pw) (PH) or |w|^2 (TDA).
+template <typename ST>
+__global__ void __launch_bounds__(256)
+k_norm_partial(const Prob* __restrict__ probs, int ph, int start) {
+  __shared__ double red[8];
+  const Prob& p = probs[blockIdx.y];
+  const KState* st = p.st;
+  if (!kphase(st, start)) return;
+  const int rb = blockIdx.x;
+  if (rb >= p.nrb) return;
+  const ST* w = (const ST*)p.w;
+  const ST* pw = (const ST*)(ph ? p.pw : p.w);
+  const int64_t r0 = (int64_t)rb * ROWBLK;
+  const int64_t r1 = min((int64_t)p.Npad, r0 + ROWBLK);
+  double s = 0.0;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += 256) {
+    const ST a = w[r], b = pw[r];
+    s += (double)a.x * (double)b.x + (double)a.y * (double)b.y;
+  }
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += red[i];
+    ((double2*)p.cpart)[rb] = mk(t, 0.0);
+  }
+}
+
+__device__ __forceinline__ double sum_norm_parts(const Prob& p) {
+  const double2* cp = (const double2*)p.cpart;
+  double s = 0.0;
+  for (int rb = 0; rb < p.nrb; ++rb) s += cp[rb].x;
+  return s;
+}
+
+// V[:, j+1] = w / beta, P[:, j+1] = pw / beta when beta^2 is usable.
+template <typename ST>
+__global__ void __launch_bounds__(256)
+k_normalize(const Prob* __restrict__ probs, int ph, int start) {
+  using R = typename RealOf<ST>::T;
+  __shared__ double sb2;
+  const Prob& p = probs[blockIdx.y];
+  const KState* st = p.st;
+  if (!kphase(st, start)) return;
+  if (threadIdx.x == 0) sb2 = sum_norm_parts(p);
+  __syncthreads();
+  const double b2 = sb2;
+  if (!(b2 > 0.0) || !isfinite(b2)) return;   // k_step_finish records the outcome
+  const R inv = (R)(1.0 / sqrt(b2));
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= p.Npad) return;
+  const int col = st->j + 1;
+  ST* V = (ST*)p.V + (int64_t)col * p.Npad;
+  V[row] = cscale(((const ST*)p.w)[row], inv);
+  if (ph) {
+    ST* P = (ST*)p.P + (int64_t)col * p.Npad;
+    P[row] = cscale(((const ST*)p.pw)[row], inv);
+  }
+}
+
+// Record alpha_j, beta_j, advance j.  fresh = 0: regular step; fresh = 1:
+// a first or replacement vector was just normalised.  One thread per problem.
+__global__ void k_step_finish(const Prob* __restrict__ probs, int nprob, int ph, int fresh) {
+  const int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= nprob) return;
+  const Prob& p = probs[ip];
+  KState* st = p.st;
+  if (!kphase(st, fresh)) return;
+  const double b2 = sum_norm_parts(p);
+  const int j = st->j;
+  if (!fresh) {
+    const double2* coef = (const double2*)p.coef;
+    const double a = coef[j].x + coef[p.ncol + j].x;
+    if (!isfinite(a) || !isfinite(b2)) { st->status = ST_NOTFINITE; return; }
+    p.alpha[j] = a;
+    st->passes += ph ? 2 : 1;
+    st->steps += 1;
+    // scale of the projected matrix for the breakdown test
+    double scale = fabs(a);
+    for (int i = st->k; i < st->l; ++i) scale = fmax(scale, fabs(p.theta[i]));
+    if (j > 0) scale = fmax(scale, fabs(p.beta[j - 1]));
+    const double tiny = 1e-26 * scale * scale + 1e-300;
+    if (ph && b2 < -1e6 * tiny) { st->status = ST_NOTPD; return; }
+    if (b2 <= tiny) {                 // invariant subspace: the chain restarts
+      p.beta[j] = 0.0;                // with a fresh vector (host-driven)
+      st->breakdown = 1;
+      return;
+    }
+    p.beta[j] = sqrt(b2);
+    st->j = j + 1;
+  } else {
+    if (!isfinite(b2)) { st->status = ST_NOTFINITE; return; }
+    if (!(b2 > 0.0)) { st->status = ph ? ST_NOTPD : ST_NOTFINITE; return; }
+    st->breakdown = 0;
+    st->passes += ph ? 1 : 0;
+    st->j = j + 1;
+  }
+  if (st->steps >= st->maxit && !st->done) { st->done = 1; st->status = ST_NOCONV; }
+}
+
+// ---------------------------------------------------------------- start vector
+// Counter-based complex Gaussian-like entries: splitmix64 of (seed, row),
+// Box-Muller on two 53-bit uniforms.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+__device__ __forceinline__ double2 hash_normal(uint64_t seed, uint64_t i) {
+  const uint64_t a = splitmix64(seed ^ splitmix64(2 * i));
+  const uint64_t b = splitmix64(seed ^ splitmix64(2 * i + 1));
+  const double u1 = ((a >> 11) + 1) * (1.0 / 9007199254740993.0);
+  const double u2 = (b >> 11) * (1.0 / 9007199254740992.0);
+  const double r = sqrt(-2.0 * log(u1));
+  double s, c;
+  sincospi(2.0 * u2, &s, &c);
+  return mk(r * c, r * s);
+}
+
+// w = v0 (if given, single problem) or random; rows >= N are zero.
+template <typename ST>
+__global__ void k_start_fill(const Prob* __restrict__ probs, uint64_t seed, const ST* __restrict__ v0) {
+  const Prob& p = probs[blockIdx.y];
+  const KState* st = p.st;
+  if (!kfresh(st)) return;
+  if (st->j >= 0) v0 = nullptr;     // replacement vectors are always random
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= p.Npad) return;
+  ST v = czero<ST>();
+  if (row < p.N) {
+    if (v0) v = v0[row];
+    else v = ccvt<ST>(hash_normal(seed + 0x51ed27ull * (uint64_t)(blockIdx.y + 1) + (uint64_t)st->restarts, row));
+  }
+  ((ST*)p.w)[row] = v;
+}
+
+// ---------------------------------------------------------------- restart
+// V2[:, i] = sum_{c < n} V[:, k0 + c] S[c, i], i < nkeep (and P2 from P).
+// grid (ceil(maxNpad/64), ceil(ncv/16), nprob), 256 threads: 64 rows x 16 cols,
+// each thread 1 row x 4 columns.
+template <typename ST>
+__global__ void __launch_bounds__(256)
+k_restart_gemm(const Prob* __restrict__ probs, int which) {
+  using R = typename RealOf<ST>::T;
+  __shared__ ST sv[32][64];
+  __shared__ R ss[32][16];
+  const Prob& p = probs[blockIdx.z];
+  const KState* st = p.st;
+  if (st->status != ST_OK) return;
+  const int k0 = st->r_k0, nkeep = st->r_nkeep;
+  const int n = st->m - k0;
+  const int i0 = blockIdx.y * 16;
+  if (i0 >= nkeep) return;
+  const int64_t r0 = (int64_t)blockIdx.x * 64;
+  if (r0 >= p.Npad) return;
+  const ST* src = (const ST*)(which ? p.P : p.V) + (int64_t)k0 * p.Npad;
+  ST* dst = (ST*)(which ? p.P2 : p.V2);
+  const int tid = threadIdx.x, rr = tid & 63, cg = tid >> 6;
+  ST acc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q] = czero<ST>();
+  for (int c0 = 0; c0 < n; c0 += 32) {
+    __syncthreads();
+    for (int e = tid; e < 32 * 64; e += 256) {
+      const int cc = e >> 6, r = e & 63;
+      const int64_t row = r0 + r;
+      sv[cc][r] = (c0 + cc < n && row < p.Npad) ? src[(int64_t)(c0 + cc) * p.Npad + row] : czero<ST>();
+    }
+    for (int e = tid; e < 32 * 16; e += 256) {
+      const int cc = e >> 4, ii = e & 15;
+      ss[cc][ii] = (c0 + cc < n && i0 + ii < nkeep) ? (R)p.S[(int64_t)(i0 + ii) * p.ncv + c0 + cc] : (R)0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int cc = 0; cc < 32; ++cc) {
+      const ST v = sv[cc][rr];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const R f = ss[cc][cg * 4 + q];
+        acc[q].x = fma(v.x, f, acc[q].x);
+        acc[q].y = fma(v.y, f, acc[q].y);
+      }
+    }
+  }
+  const int64_t row = r0 + rr;
+  if (row < p.Npad) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = i0 + cg * 4 + q;
+      if (i < nkeep) dst[(int64_t)i * p.Npad + row] = acc[q];
+    }
+  }
+}
+
+// V[:, k0+i] = V2[:, i]; V[:, k0+nkeep] = V[:, m]; same for P.
+template <typename ST>
+__global__ void k_restart_copy(const Prob* __restrict__ probs, int ph) {
+  const Prob& p = probs[blockIdx.y];
+  const KState* st = p.st;
+  if (st->status != ST_OK) return;
+  const int k0 = st->r_k0, nkeep = st->r_nkeep, m = st->m;
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= p.Npad) return;
+  ST* V = (ST*)p.V;
+  const ST* V2 = (const ST*)p.V2;
+  const ST vm = V[(int64_t)m * p.Npad + row];
+  for (int i = 0; i < nkeep; ++i) V[(int64_t)(k0 + i) * p.Npad + row] = V2[(int64_t)i * p.Npad + row];
+  V[(int64_t)(k0 + nkeep) * p.Npad + row] = vm;
+  if (ph) {
+    ST* P = (ST*)p.P;
+    const ST* P2 = (const ST*)p.P2;
+    const ST pm = P[(int64_t)m * p.Npad + row];
+    for (int i = 0; i < nkeep; ++i) P[(int64_t)(k0 + i) * p.Npad + row] = P2[(int64_t)i * p.Npad + row];
+    P[(int64_t)(k0 + nkeep) * p.Npad + row] = pm;
+  }
+}
+
+// Twins of the kept vectors y_i (i < l = k0 + nkeep):
+//   t_i = i P[:, i] / w_i,  M+ t_i = i (theta_i y_i + b_i v_l) / w_i,  w_i = sqrt(theta_i)
+// (M+ t = i M- M+ y / w and M- M+ y = theta y + b v_l by the Krylov relation).
+template <typename ST>
+__global__ void k_twins(const Prob* __restrict__ probs) {
+  using R = typename RealOf<ST>::T;
+  const Prob& p = probs[blockIdx.y];
+  const KState* st = p.st;
+  if (st->status != ST_OK) return;
+  const int l = st->r_k0 + st->r_nkeep;
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= p.Npad) return;
+  const ST* V = (const ST*)p.V;
+  ST* Vw = (ST*)p.V;
+  ST* Pw = (ST*)p.P;
+  const ST vl = V[(int64_t)l * p.Npad + row];
+  const int tw0 = p.ncv + 1;
+  for (int i = 0; i < l; ++i) {
+    const double th = p.theta[i];
+    if (!(th > 0.0)) continue;
+    const double om = sqrt(th);
+    const R inv = (R)(1.0 / om);
+    const ST pi = ((const ST*)p.P)[(int64_t)i * p.Npad + row];
+    const ST yi = V[(int64_t)i * p.Npad + row];
+    ST t;   // i * pi / om
+    t.x = -pi.y * inv; t.y = pi.x * inv;
+    Vw[(int64_t)(tw0 + i) * p.Npad + row] = t;
+    const R th_r = (R)th, b = (R)p.barrow[i];
+    ST q;   // theta y + b v_l
+    q.x = th_r * yi.x + b * vl.x;
+    q.y = th_r * yi.y + b * vl.y;
+    ST pt;
+    pt.x = -q.y * inv; pt.y = q.x * inv;
+    Pw[(int64_t)(tw0 + i) * p.Npad + row] = pt;
+  }
+}
+
+__global__ void k_restart_commit(const Prob* __restrict__ probs, int nprob, int ph) {
+  const int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= nprob) return;
+  const Prob& p = probs[ip];
+  KState* st = p.st;
+  if (st->status != ST_OK) return;
+  const int k0 = st->r_k0;
+  st->k = k0 + st->r_nl;
+  st->l = k0 + st->r_nkeep;
+  st->j = st->l;
+  st->ntw = ph ? st->l : 0;
+  st->restarts += 1;
+  if (st->k >= st->nev) st->done = 1;
+  else if (st->steps >= st->maxit) { st->done = 1; st->status = ST_NOCONV; }
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename ST>
+void launch_step_cgs(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t maxNpad, int ncol,
+                     int pass, cudaStream_t s) {
+  // pass: 0/1 regular step passes; 2/3 the same for a fresh (replacement) vector
+  const int newvec = pass >= 2 ? 1 : 0;
+  const int ps = pass & 1;
+  k_cgs_dot<ST><<<dim3((ncol + 7) / 8, maxnrb, nprob), 256, 0, s>>>(dprobs, ph, newvec);
+  k_cgs_coef<<<dim3((ncol + 255) / 256, nprob), 256, 0, s>>>(dprobs, ph, ps, newvec);
+  k_cgs_update<ST><<<dim3((unsigned)((maxNpad + 127) / 128), nprob), 128, 0, s>>>(dprobs, ph, ps, newvec);
+}
+
+template <typename ST>
+void launch_step_normalize(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t maxNpad,
+                           int start, cudaStream_t s) {
+  // start: 0 regular step, 1 fresh (first or replacement) vector
+  k_norm_partial<ST><<<dim3(maxnrb, nprob), 256, 0, s>>>(dprobs, ph, start);
+  k_normalize<ST><<<dim3((unsigned)((maxNpad + 255) / 256), nprob), 256, 0, s>>>(dprobs, ph, start);
+  k_step_finish<<<(nprob + 127) / 128, 128, 0, s>>>(dprobs, nprob, ph, start);
+}
+
+template <typename ST>
+void launch_start_vector(const Prob* dprobs, int nprob, int64_t maxNpad, uint64_t seed, const void* v0,
+                         cudaStream_t s) {
+  // fills w for every problem that needs a fresh vector
+  k_start_fill<ST><<<dim3((unsigned)((maxNpad + 255) / 256), nprob), 256, 0, s>>>(
+      dprobs, seed, (const ST*)v0);
+}
+
+template <typename ST>
+void launch_restart(const Prob* dprobs, int nprob, int ph, int64_t maxNpad, int ncv, cudaStream_t s) {
+  const unsigned gx = (unsigned)((maxNpad + 63) / 64);
+  k_restart_gemm<ST><<<dim3(gx, (ncv + 15) / 16, nprob), 256, 0, s>>>(dprobs, 0);
+  if (ph) k_restart_gemm<ST><<<dim3(gx, (ncv + 15) / 16, nprob), 256, 0, s>>>(dprobs, 1);
+  const unsigned gr = (unsigned)((maxNpad + 255) / 256);
+  k_restart_copy<ST><<<dim3(gr, nprob), 256, 0, s>>>(dprobs, ph);
+  if (ph) k_twins<ST><<<dim3(gr, nprob), 256, 0, s>>>(dprobs);
+  k_restart_commit<<<(nprob + 127) / 128, 128, 0, s>>>(dprobs, nprob, ph);
+}
+
+#define INST(ST)                                                                                   \
+  template void launch_step_cgs<ST>(const Prob*, int, int, int, int64_t, int, int, cudaStream_t); \
+  template void launch_step_normalize<ST>(const Prob*, int, int, int, int64_t, int, cudaStream_t); \
+  template void launch_start_vector<ST>(const Prob*, int, int64_t, uint64_t, const void*,         \
+                                        cudaStream_t);                                             \
+  template void launch_restart<ST>(const Prob*, int, int, int64_t, int, cudaStream_t);
+INST(float2)
+INST(double2)
+#undef INST
+
+}  // namespace bse

@@ -1,0 +1,369 @@
+// Structured products with the packed A and B (BSE Eq. 1 blocks).
+//
+// The hot kernel k_prod_tiles streams every stored upper-triangle tile of A
+// (and of B) exactly once per product and uses it for both block rows:
+//     y_I += A_IJ x_J + s B_IJ conj(x_J)
+//     y_J += A_IJ^H x_I + s B_IJ^T conj(x_I)        (I < J)
+// because A = A^H and B = B^T.  This is the matrix-vector product that the
+// paper identifies as the most expensive step of the iterative solver
+// (Sec. 2.2.2, last paragraph).  Each tile writes its two partial block-row
+// results into a scratch buffer part[I][J][:] (slot (I,J) receives the
+// contribution of column block J to row block I), and k_prod_reduce sums the
+// nT slots of every block row: no atomics, deterministic rounding order.
+//
+// k_prod_rowblock is the wide-block variant (k columns, GEMM-like): one CTA
+// owns an output block row and reads tile (I,J) or the transpose of (J,I).
+#include "bse_internal.cuh"
+
+namespace bse {
+
+template <typename R> struct Acc;
+template <> struct Acc<float> { using T = float2; };
+template <> struct Acc<double> { using T = double2; };
+
+template <typename T>
+__device__ __forceinline__ T shfl_xor_c(T v, int m) {
+  v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+  v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+  return v;
+}
+
+// Resolve the input / output vectors of a product for problem p.
+// Returns false if the problem takes no part in this launch.
+template <typename ST, typename R>
+__device__ __forceinline__ bool prod_operands(const Prob& p, int mode, const GenericIO& io,
+                                              const ST*& x, ST*& y, R& sB) {
+  const KState* st = p.st;
+  if (mode == PM_GENERIC) {
+    x = (const ST*)io.xa; y = (ST*)io.y; sB = (R)io.sB; return true;
+  }
+  if (st->done || st->status != ST_OK) return false;
+  const int j = st->j;
+  const bool fresh = j < 0 || st->breakdown;
+  switch (mode) {
+    case PM_STEP_MMINUS:
+      if (fresh || j >= p.ncv) return false;
+      x = (const ST*)p.P + (int64_t)j * p.Npad; y = (ST*)p.w; sB = (R)-1; return true;
+    case PM_STEP_MPLUS:
+      if (fresh || j >= p.ncv) return false;
+      x = (const ST*)p.w; y = (ST*)p.pw; sB = (R)1; return true;
+    case PM_STEP_A:
+      if (fresh || j >= p.ncv) return false;
+      x = (const ST*)p.V + (int64_t)j * p.Npad; y = (ST*)p.w; sB = (R)0; return true;
+    case PM_START_MPLUS:
+      if (!fresh) return false;
+      x = (const ST*)p.w; y = (ST*)p.pw; sB = (R)1; return true;
+  }
+  return false;
+}
+
+// One CTA processes a contiguous chunk of tiles of the global job list.
+template <typename ST, typename R, bool HASB>
+__global__ void __launch_bounds__(PROD_THREADS, 1)
+k_prod_tiles(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs, int njobs,
+             int mode, GenericIO io) {
+  using CT = typename Acc<R>::T;
+  __shared__ CT xc[2][TS];   // column block J: x, s*conj(x)
+  __shared__ CT xr[2][TS];   // row block I
+  __shared__ CT red[8][TS];  // column reduction across warps
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int per = (njobs + gridDim.x - 1) / gridDim.x;
+  const int t0 = blockIdx.x * per;
+  const int t1 = min(njobs, t0 + per);
+  for (int t = t0; t < t1; ++t) {
+    const TileJob jb = jobs[t];
+    const Prob& p = probs[jb.prob];
+    const ST* x; ST* yout; R sB;
+    if (!prod_operands<ST, R>(p, mode, io, x, yout, sB)) continue;   // uniform per CTA
+    const bool diag = (jb.I == jb.J);
+    __syncthreads();                       // smem of the previous tile is free
+    if (tid < TS) {
+      CT a = ccvt<CT>(x[(int64_t)jb.J * TS + tid]);
+      xc[0][tid] = a;
+      xc[1][tid] = cscale(conjc(a), sB);
+    } else {
+      const int r = tid - TS;
+      CT a = ccvt<CT>(x[(int64_t)jb.I * TS + r]);
+      xr[0][r] = a;
+      xr[1][r] = cscale(conjc(a), sB);
+    }
+    __syncthreads();
+    const ST* At = (const ST*)p.A + (int64_t)jb.t * (TS * TS);
+    const ST* Bt = HASB ? (const ST*)p.B + (int64_t)jb.t * (TS * TS) : nullptr;
+    CT racc[8], cacc[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) cacc[b] = czero<CT>();
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int r = ty + 16 * a;
+      ST av[8], bv[8];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        av[b] = __ldg(At + r * TS + tx + 16 * b);
+        if (HASB) bv[b] = __ldg(Bt + r * TS + tx + 16 * b);
+      }
+      CT ra = czero<CT>();
+      const CT xra = xr[0][r];
+      const CT xrb = xr[1][r];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const int c = tx + 16 * b;
+        const CT A = ccvt<CT>(av[b]);
+        cfma(ra, A, xc[0][c]);               // (A_IJ x_J)_r
+        if (!diag) cfmac(cacc[b], A, xra);   // (A_IJ^H x_I)_c
+        if (HASB) {
+          const CT Bv = ccvt<CT>(bv[b]);
+          cfma(ra, Bv, xc[1][c]);            // s (B_IJ conj x_J)_r
+          if (!diag) cfma(cacc[b], Bv, xrb); // s (B_IJ^T conj x_I)_c
+        }
+      }
+      racc[a] = ra;
+    }
+    // ---- row sums: reduce-scatter over the 16 tx lanes (xor 8, 4, 2, 1)
+    {
+      const bool u8 = tx & 8;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        CT send = u8 ? racc[q] : racc[q + 4];
+        CT keep = u8 ? racc[q + 4] : racc[q];
+        racc[q] = cadd(keep, shfl_xor_c(send, 8));
+      }
+      const bool u4 = tx & 4;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        CT send = u4 ? racc[q] : racc[q + 2];
+        CT keep = u4 ? racc[q + 2] : racc[q];
+        racc[q] = cadd(keep, shfl_xor_c(send, 4));
+      }
+      const bool u2 = tx & 2;
+      {
+        CT send = u2 ? racc[0] : racc[1];
+        CT keep = u2 ? racc[1] : racc[0];
+        racc[0] = cadd(keep, shfl_xor_c(send, 2));
+      }
+      racc[0] = cadd(racc[0], shfl_xor_c(racc[0], 1));
+      if ((tx & 1) == 0) {
+        const int a = (tx >> 1) & 7;
+        const int r = ty + 16 * a;
+        CT* part = (CT*)p.part;
+        part[((int64_t)jb.I * p.nT + jb.J) * TS + r] = racc[0];
+      }
+    }
+    if (!diag) {
+      // ---- column sums: pair the two ty of a warp (xor 16), then across warps
+      const bool up = lane & 16;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        CT send = up ? cacc[q] : cacc[q + 4];
+        CT keep = up ? cacc[q + 4] : cacc[q];
+        cacc[q] = cadd(keep, shfl_xor_c(send, 16));
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) red[warp][tx + 16 * (q + (up ? 4 : 0))] = cacc[q];
+      __syncthreads();
+      if (tid < TS) {
+        CT s = red[0][tid];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) s = cadd(s, red[w][tid]);
+        CT* part = (CT*)p.part;
+        part[((int64_t)jb.J * p.nT + jb.I) * TS + tid] = s;
+      }
+    }
+  }
+}
+
+// y[I*TS + r] = sum_J part[I][J][r]; grid (maxnT, nprob).
+template <typename ST, typename R>
+__global__ void __launch_bounds__(256)
+k_prod_reduce(const Prob* __restrict__ probs, int mode, GenericIO io) {
+  using CT = typename Acc<R>::T;
+  __shared__ CT half[TS];
+  const Prob& p = probs[blockIdx.y];
+  const int I = blockIdx.x;
+  if (I >= p.nT) return;
+  const ST* x; ST* y; R sB;
+  if (!prod_operands<ST, R>(p, mode, io, x, y, sB)) return;
+  const int r = threadIdx.x & (TS - 1), h = threadIdx.x >> 7;
+  const CT* part = (const CT*)p.part + (int64_t)I * p.nT * TS;
+  CT acc = czero<CT>();
+  for (int J = h; J < p.nT; J += 2) acc = cadd(acc, part[(int64_t)J * TS + r]);
+  if (h == 1) half[r] = acc;
+  __syncthreads();
+  if (h == 0) {
+    acc = cadd(acc, half[r]);
+    y[(int64_t)I * TS + r] = ccvt<ST>(acc);
+  }
+}
+
+// ---------------------------------------------------------------- wide blocks
+// Y[:, c0:c0+16] of block row I = sum_J Ablk(I,J) XA_J + sB Bblk(I,J) XB_J,
+// Ablk(I,J) = tile(I,J) for J >= I, tile(J,I)^H otherwise; Bblk uses ^T.
+// XA, XB, Y: compute-type complex, column-major, Npad rows.
+constexpr int RB_Q = 16;   // q-chunk staged in shared memory
+template <typename ST, typename R, bool HASB>
+__global__ void __launch_bounds__(256)
+k_prod_rowblock(const Prob* __restrict__ probs, int prob, const typename Acc<R>::T* __restrict__ xa,
+                const typename Acc<R>::T* __restrict__ xb, int ldx, R sB,
+                typename Acc<R>::T* __restrict__ y, int ldy, int K) {
+  using CT = typename Acc<R>::T;
+  extern __shared__ unsigned char smem_raw[];
+  CT* sA = (CT*)smem_raw;                 // [RB_Q][TS]
+  CT* sB_ = sA + RB_Q * TS;               // [RB_Q][TS]
+  CT* sXa = sB_ + RB_Q * TS;              // [RB_Q][16]
+  CT* sXb = sXa + RB_Q * 16;              // [RB_Q][16]
+  const Prob& p = probs[prob];
+  const int I = blockIdx.x, c0 = blockIdx.y * 16;
+  const int tid = threadIdx.x;
+  const int c = tid >> 4, rr = tid & 15;
+  const int nT = p.nT;
+  CT acc[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) acc[a] = czero<CT>();
+  for (int J = 0; J < nT; ++J) {
+    const bool upper = J >= I;
+    const int ti = upper ? I : J, tj = upper ? J : I;
+    const int64_t tix = (int64_t)ti * nT - (int64_t)ti * (ti - 1) / 2 + (tj - ti);
+    const ST* At = (const ST*)p.A + tix * (TS * TS);
+    const ST* Bt = HASB ? (const ST*)p.B + tix * (TS * TS) : nullptr;
+    for (int q0 = 0; q0 < TS; q0 += RB_Q) {
+      __syncthreads();
+      if (upper) {
+        // Ablk[r][q] = tile[r][q]
+        for (int e = tid; e < TS * RB_Q; e += 256) {
+          const int qq = e & (RB_Q - 1), r = e >> 4;
+          sA[qq * TS + r] = ccvt<CT>(At[r * TS + q0 + qq]);
+          if (HASB) sB_[qq * TS + r] = ccvt<CT>(Bt[r * TS + q0 + qq]);
+        }
+      } else {
+        // Ablk[r][q] = conj(tile[q][r]); Bblk[r][q] = tile[q][r]
+        for (int e = tid; e < TS * RB_Q; e += 256) {
+          const int r = e & (TS - 1), qq = e >> 7;
+          sA[qq * TS + r] = conjc(ccvt<CT>(At[(q0 + qq) * TS + r]));
+          if (HASB) sB_[qq * TS + r] = ccvt<CT>(Bt[(q0 + qq) * TS + r]);
+        }
+      }
+      {
+        const int qq = tid & (RB_Q - 1), cc = tid >> 4;
+        const int64_t row = (int64_t)J * TS + q0 + qq;
+        CT va = czero<CT>(), vb = czero<CT>();
+        if (c0 + cc < K) {
+          va = xa[(int64_t)(c0 + cc) * ldx + row];
+          vb = xb ? xb[(int64_t)(c0 + cc) * ldx + row] : conjc(va);
+        }
+        sXa[qq * 16 + cc] = va;
+        sXb[qq * 16 + cc] = cscale(vb, sB);
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int qq = 0; qq < RB_Q; ++qq) {
+        const CT xv = sXa[qq * 16 + c];
+        const CT xw = sXb[qq * 16 + c];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          cfma(acc[a], sA[qq * TS + rr + 16 * a], xv);
+          if (HASB) cfma(acc[a], sB_[qq * TS + rr + 16 * a], xw);
+        }
+      }
+    }
+  }
+  if (c0 + c < K) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a) y[(int64_t)(c0 + c) * ldy + (int64_t)I * TS + rr + 16 * a] = acc[a];
+  }
+}
+
+// ---------------------------------------------------------------- packing
+// Pack the tiles (I, J >= I) of block row I from `rows` (TS rows of the full
+// row-major matrix starting at row I*TS, leading dimension N).
+template <typename TIn, typename TSt>
+__global__ void __launch_bounds__(256)
+k_pack_row(const TIn* __restrict__ rows, int64_t N, int nT, int I, int herm, TSt* __restrict__ dst) {
+  const int J = I + blockIdx.x;
+  const int64_t t = (int64_t)I * nT - (int64_t)I * (I - 1) / 2 + (J - I);
+  TSt* out = dst + t * (TS * TS);
+  for (int e = threadIdx.x; e < TS * TS; e += 256) {
+    const int r = e >> 7, c = e & (TS - 1);
+    const int64_t gi = (int64_t)I * TS + r, gj = (int64_t)J * TS + c;
+    TSt v = czero<TSt>();
+    if (gi < N && gj < N) {
+      if (I != J || r < c) {
+        v = ccvt<TSt>(rows[(int64_t)r * N + gj]);
+      } else if (r == c) {
+        v = ccvt<TSt>(rows[(int64_t)r * N + gj]);
+        if (herm) v.y = 0;
+      } else {  // lower half of a diagonal tile: mirror of (c, r)
+        v = ccvt<TSt>(rows[(int64_t)c * N + (int64_t)I * TS + r]);
+        if (herm) v.y = -v.y;
+      }
+    }
+    out[e] = v;
+  }
+}
+
+template <typename TIn, typename TSt>
+void launch_pack_row(const TIn* rows, int64_t N, int nT, int I, int herm, TSt* dst, cudaStream_t s) {
+  k_pack_row<TIn, TSt><<<nT - I, 256, 0, s>>>(rows, N, nT, I, herm, dst);
+}
+
+template void launch_pack_row<double2, double2>(const double2*, int64_t, int, int, int, double2*, cudaStream_t);
+template void launch_pack_row<float2, float2>(const float2*, int64_t, int, int, int, float2*, cudaStream_t);
+
+// ---------------------------------------------------------------- launchers
+static int g_num_sms = 0;
+static int num_sms() {
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+template <typename ST, typename R>
+void launch_product(const Prob* dprobs, const TileJob* jobs, int njobs, int nprob, int maxnT,
+                    int mode, int K, const GenericIO* io_host, bool hasB, cudaStream_t s) {
+  GenericIO io{};
+  if (io_host) io = *io_host;
+  (void)K;
+  int grid = 2 * num_sms();
+  if (grid > njobs) grid = njobs;
+  if (grid < 1) grid = 1;
+  if (hasB)
+    k_prod_tiles<ST, R, true><<<grid, PROD_THREADS, 0, s>>>(dprobs, jobs, njobs, mode, io);
+  else
+    k_prod_tiles<ST, R, false><<<grid, PROD_THREADS, 0, s>>>(dprobs, jobs, njobs, mode, io);
+  k_prod_reduce<ST, R><<<dim3(maxnT, nprob), 256, 0, s>>>(dprobs, mode, io);
+}
+
+template void launch_product<double2, double>(const Prob*, const TileJob*, int, int, int, int, int,
+                                              const GenericIO*, bool, cudaStream_t);
+template void launch_product<float2, float>(const Prob*, const TileJob*, int, int, int, int, int,
+                                            const GenericIO*, bool, cudaStream_t);
+
+template <typename ST, typename R>
+void launch_rowblock(const Prob* dprobs, int prob, int nT, const void* xa, const void* xb, int ldx,
+                     double sB, void* y, int ldy, int K, bool hasB, cudaStream_t s) {
+  using CT = typename Acc<R>::T;
+  const size_t sm = (size_t)(2 * RB_Q * TS + 2 * RB_Q * 16) * sizeof(CT);
+  dim3 grid(nT, (K + 15) / 16);
+  if (hasB) {
+    cudaFuncSetAttribute(k_prod_rowblock<ST, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_prod_rowblock<ST, R, true><<<grid, 256, sm, s>>>(dprobs, prob, (const CT*)xa, (const CT*)xb, ldx,
+                                                       (R)sB, (CT*)y, ldy, K);
+  } else {
+    cudaFuncSetAttribute(k_prod_rowblock<ST, R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_prod_rowblock<ST, R, false><<<grid, 256, sm, s>>>(dprobs, prob, (const CT*)xa, (const CT*)xb, ldx,
+                                                        (R)sB, (CT*)y, ldy, K);
+  }
+}
+
+template void launch_rowblock<double2, double>(const Prob*, int, int, const void*, const void*, int,
+                                               double, void*, int, int, bool, cudaStream_t);
+template void launch_rowblock<float2, double>(const Prob*, int, int, const void*, const void*, int,
+                                              double, void*, int, int, bool, cudaStream_t);
+template void launch_rowblock<float2, float>(const Prob*, int, int, const void*, const void*, int,
+                                             double, void*, int, int, bool, cudaStream_t);
+
+}  // namespace bse

@@ -1,0 +1,141 @@
+"""GPU parity of the iterative solver against the dense FP64 oracle.
+
+Eigenvalues are unique and compared one by one; eigenvectors are unique up to
+a phase and are compared through |z_gpu^H Omega z_oracle| (PH) or
+|x_gpu^H x_oracle| (TDA), plus residuals and the Omega-normalisation."""
+import numpy as np
+import pytest
+
+import oracle as O
+from tests.gpu_common import omega_metric_apply, problem
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _solver(A, B=None):
+    from paper_2504_10096_gb300 import bse
+    return bse.Solver(torch.from_numpy(A).cuda(), None if B is None else torch.from_numpy(B).cuda())
+
+
+@pytest.mark.parametrize("n,nev", [(300, 8), (515, 12)])
+def test_tda_fp64(n, nev):
+    A, _ = problem(n, "c128", form="tda", seed=n)
+    s = _solver(A)
+    vals, vecs, nconv = s.solve(nev, tol=1e-12)
+    lam, Xo = O.tda_lowest(A, nev)
+    assert nconv == nev
+    np.testing.assert_allclose(vals, lam, rtol=1e-10, atol=0)
+    X = vecs.cpu().numpy()
+    ov = np.abs(np.einsum("ij,ij->j", X.conj(), Xo))
+    np.testing.assert_allclose(ov, 1.0, atol=1e-8)
+    assert O.relative_residuals_tda(A, vals, X).max() < 1e-11
+    assert s.stats()["max_residual"] < 1e-11
+    s.close()
+
+
+@pytest.mark.parametrize("n,nev", [(300, 10), (515, 16)])
+def test_ph_fp64(n, nev):
+    A, B = problem(n, "c128", seed=n + 1)
+    s = _solver(A, B)
+    vals, vecs, nconv = s.solve(nev, tol=1e-12)
+    om, Xo, Yo = O.ph_lowest(A, B, nev)
+    assert nconv == nev
+    np.testing.assert_allclose(vals, om, rtol=1e-10, atol=0)
+    Z = vecs.cpu().numpy()
+    Zo = np.vstack([Xo, Yo])
+    # Omega-normalisation and overlap with the oracle's vectors
+    jn = np.real(np.einsum("ij,ij->j", Z.conj(), omega_metric_apply(Z)))
+    np.testing.assert_allclose(jn, 1.0, atol=1e-10)
+    ov = np.abs(np.einsum("ij,ij->j", Z.conj(), omega_metric_apply(Zo)))
+    np.testing.assert_allclose(ov, 1.0, atol=1e-8)
+    X, Y = Z[:n], Z[n:]
+    assert O.relative_residuals_ph(A, B, vals, X, Y).max() < 1e-11
+    # Eq. 7: the -omega partner (conj Y; conj X) needs no extra solve
+    H = O.bse_hamiltonian(A, B)
+    Zm = np.vstack([Y.conj(), X.conj()])
+    assert np.linalg.norm(H @ Zm + Zm * vals) / np.linalg.norm(Zm) < 1e-10
+    s.close()
+
+
+def test_ph_mixed_c64():
+    n, nev = 600, 12
+    A, B = problem(n, "c64", seed=17)
+    s = _solver(A, B)
+    vals, vecs, nconv = s.solve(nev, tol=1e-6)
+    om, _, _ = O.ph_lowest(A.astype(np.complex128), B.astype(np.complex128), nev)
+    assert nconv == nev
+    np.testing.assert_allclose(vals, om, rtol=1e-6, atol=0)
+    assert s.stats()["max_residual"] < 1e-5
+    s.close()
+
+
+def test_b_zero_equals_tda():
+    """B = 0: the PH solve returns the TDA spectrum (Sec. 1)."""
+    n, nev = 256, 6
+    A, _ = problem(n, "c128", form="tda", seed=21)
+    s = _solver(A, np.zeros_like(A))
+    vals, _, _ = s.solve(nev, tol=1e-12)
+    lam, _ = O.tda_lowest(A, nev)
+    np.testing.assert_allclose(vals, lam, rtol=1e-10)
+    s.close()
+
+
+def test_diagonal_complex_coupling_closed_form():
+    """A = diag(a), B = diag(b): omega_i = sqrt(a_i^2 - |b_i|^2) (decoupled 2x2)."""
+    rng = np.random.default_rng(4)
+    n, nev = 200, 7
+    a = rng.uniform(1.5, 10.0, n)
+    b = rng.uniform(0.0, 0.4, n) * np.exp(2j * np.pi * rng.uniform(size=n))
+    s = _solver(np.diag(a).astype(np.complex128), np.diag(b))
+    vals, _, _ = s.solve(nev, tol=1e-12)
+    np.testing.assert_allclose(vals, np.sort(np.sqrt(a * a - np.abs(b) ** 2))[:nev], rtol=1e-10)
+    s.close()
+
+
+def test_degenerate_scalar_blocks():
+    """A = aI, B = bI: every omega equals sqrt(a^2 - |b|^2); each Krylov chain
+    breaks down at once and the solver restarts it with fresh vectors."""
+    n, nev = 48, 5
+    a, b = 2.0, 0.5 * np.exp(0.7j)
+    s = _solver(a * np.eye(n, dtype=np.complex128), b * np.eye(n, dtype=np.complex128))
+    vals, _, nconv = s.solve(nev, tol=1e-12)
+    assert nconv == nev
+    np.testing.assert_allclose(vals, np.sqrt(a * a - abs(b) ** 2), rtol=1e-12)
+    s.close()
+
+
+def test_not_positive_definite_is_reported():
+    from paper_2504_10096_gb300 import bse
+    n = 64
+    A = np.eye(n, dtype=np.complex128)
+    B = 2.0 * np.eye(n, dtype=np.complex128)
+    s = _solver(A, B)
+    with pytest.raises(bse.BSEError) as ei:
+        s.solve(4, tol=1e-10)
+    assert ei.value.status == bse.BSE_ENOTPD
+    s.close()
+
+
+def test_invalid_arguments():
+    from paper_2504_10096_gb300 import bse
+    A, B = problem(130, "c128", seed=2)
+    s = _solver(A, B)
+    rc, _, _ = bse.bse_solve(s.h, 0, 1e-10)
+    assert rc == bse.BSE_EINVAL
+    rc, _, _ = bse.bse_solve(s.h, 131, 1e-10)
+    assert rc == bse.BSE_EINVAL
+    assert bse.bse_backward(s.h, np.zeros(3).ctypes.data, bse.BSE_HOST, 1, 1) == bse.BSE_ESTATE
+    s.close()
+
+
+def test_config0_tda_n2000():
+    """Workload config 0: TDA, N = 2000, lowest 20, FP64."""
+    from synthetic import CONFIGS, make_problem
+    spec = CONFIGS[0]
+    p = make_problem(spec)
+    s = _solver(p["A"])
+    vals, vecs, nconv = s.solve(spec.nev, tol=1e-12)
+    lam, _ = O.tda_lowest(p["A"], spec.nev)
+    np.testing.assert_allclose(vals, lam, rtol=1e-10, atol=0)
+    s.close()

@@ -101,6 +101,7 @@ typedef struct bse_stats {
   double max_residual;   /* max FP64 relative residual of returned pairs      */
   double ms_total;       /* device time of the last solve (CUDA events)       */
   double ms_product;     /* device time inside the structured products        */
+  int64_t launches;      /* CUDA kernels launched by the last solve           */
 } bse_stats;
 
 /* Human-readable message for a status code (static storage). */

@@ -37,7 +37,8 @@ class bse_solve_opts(ctypes.Structure):
 class bse_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("passes", ctypes.c_int64), ("restarts", ctypes.c_int64),
                 ("nconv", ctypes.c_int), ("max_residual", ctypes.c_double),
-                ("ms_total", ctypes.c_double), ("ms_product", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("ms_product", ctypes.c_double),
+                ("launches", ctypes.c_int64)]
 
 
 class BSEError(RuntimeError):

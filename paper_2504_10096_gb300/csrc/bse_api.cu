@@ -428,6 +428,7 @@ int solve_impl(bse_handle* h, int nev, double tol, const bse_solve_opts* opts, d
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, h->stream);
+  const long long launches0 = launch_counter();
   Driver<ST> drv(h);
   rc = drv.iterate(seed, v0);
   if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
@@ -470,6 +471,7 @@ int solve_impl(bse_handle* h, int nev, double tol, const bse_solve_opts* opts, d
   h->stats.max_residual = maxres;
   h->stats.ms_total = ms;
   h->stats.ms_product = h->ms_product;
+  h->stats.launches = launch_counter() - launches0;
   h->solved = true;
   return worst;
 }
@@ -543,6 +545,7 @@ int apply_impl(bse_handle* h, int op, int k, const void* X, void* Y) {
       if ((rc = alloc_solve(h, std::min<int64_t>(q.N, 8) > 1 ? (int)std::min<int64_t>(q.N, 8) : 1))) return rc;
       if ((rc = upload_probs(h))) return rc;
     }
+    count_launch();
     k_pad_in<ST><<<dim3((unsigned)((Npad + 255) / 256), 1), 256, 0, h->stream>>>(
         (const ST*)X, N, N, Npad, 1, 0, (ST*)q.w);
     GenericIO io{};
@@ -575,16 +578,19 @@ int apply_impl(bse_handle* h, int op, int k, const void* X, void* Y) {
   double sB = 0.0;
   const void* xb = nullptr;
   if (op == BSE_OP_H) {
+    count_launch();
     k_hz_in<ST, CT><<<g, 256, 0, h->stream>>>((const ST*)X, N, Npad, k, XA, XB);
     sB = 1.0;
     xb = XB;
   } else {
+    count_launch();
     k_cvt_pad<ST, CT><<<g, 256, 0, h->stream>>>((const ST*)X, N, Npad, k, XA);
     sB = op == BSE_OP_A ? 0.0 : (op == BSE_OP_MPLUS ? 1.0 : -1.0);
     xb = nullptr;  // conj(XA)
   }
   launch_rowblock<ST, R>(h->dprobs, 0, q.nT, XA, xb, (int)Npad, sB, U, (int)Npad, kc,
                          hasB && op != BSE_OP_A, h->stream);
+  count_launch();
   k_hz_out<ST, CT><<<dim3((unsigned)((N + 255) / 256), k), 256, 0, h->stream>>>(U, N, Npad, k, op, (ST*)Y);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));

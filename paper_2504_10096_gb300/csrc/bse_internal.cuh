@@ -81,6 +81,7 @@ struct KState {
   int breakdown;
   // pending restart decision (written by k_lock_decide, consumed by restart kernels)
   int r_k0, r_nl, r_nkeep, r_pkeep;
+  int r_go;     // 1 between a restart decision and its commit (active problems only)
   long long steps, passes, restarts, maxit;
   double tol, lock_tol;
   double beta_last;   // beta_{m-1}: coupling of the last vector to V[:, m]
@@ -134,6 +135,13 @@ struct GenericIO {     // explicit operands for PM_GENERIC (single problem)
   double sB;           // sign of the B term (0 disables it)
   void* y; int ldy;    // output (compute type) Npad x K
 };
+
+// Kernel launches issued by this process (reported per solve in bse_stats).
+inline long long& launch_counter() {
+  static long long c = 0;
+  return c;
+}
+inline void count_launch(int n = 1) { launch_counter() += n; }
 
 // ---------------------------------------------------------------- launchers
 // packing (k_product.cu): tiles (I, J >= I) of block row I from TS rows

@@ -274,7 +274,7 @@ k_restart_gemm(const Prob* __restrict__ probs, int which) {
   __shared__ R ss[32][16];
   const Prob& p = probs[blockIdx.z];
   const KState* st = p.st;
-  if (st->status != ST_OK) return;
+  if (st->status != ST_OK || !st->r_go) return;   // decided in this restart only
   const int k0 = st->r_k0, nkeep = st->r_nkeep;
   const int n = st->m - k0;
   const int i0 = blockIdx.y * 16;
@@ -325,7 +325,7 @@ template <typename ST>
 __global__ void k_restart_copy(const Prob* __restrict__ probs, int ph) {
   const Prob& p = probs[blockIdx.y];
   const KState* st = p.st;
-  if (st->status != ST_OK) return;
+  if (st->status != ST_OK || !st->r_go) return;   // decided in this restart only
   const int k0 = st->r_k0, nkeep = st->r_nkeep, m = st->m;
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= p.Npad) return;
@@ -351,7 +351,7 @@ __global__ void k_twins(const Prob* __restrict__ probs) {
   using R = typename RealOf<ST>::T;
   const Prob& p = probs[blockIdx.y];
   const KState* st = p.st;
-  if (st->status != ST_OK) return;
+  if (st->status != ST_OK || !st->r_go) return;   // decided in this restart only
   const int l = st->r_k0 + st->r_nkeep;
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= p.Npad) return;
@@ -385,13 +385,14 @@ __global__ void k_restart_commit(const Prob* __restrict__ probs, int nprob, int 
   if (ip >= nprob) return;
   const Prob& p = probs[ip];
   KState* st = p.st;
-  if (st->status != ST_OK) return;
+  if (st->status != ST_OK || !st->r_go) return;   // decided in this restart only
   const int k0 = st->r_k0;
   st->k = k0 + st->r_nl;
   st->l = k0 + st->r_nkeep;
   st->j = st->l;
   st->ntw = ph ? st->l : 0;
   st->restarts += 1;
+  st->r_go = 0;
   if (st->k >= st->nev) st->done = 1;
   else if (st->steps >= st->maxit) { st->done = 1; st->status = ST_NOCONV; }
 }
@@ -401,6 +402,7 @@ template <typename ST>
 void launch_step_cgs(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t maxNpad, int ncol,
                      int pass, cudaStream_t s) {
   // pass: 0/1 regular step passes; 2/3 the same for a fresh (replacement) vector
+  count_launch(3);
   const int newvec = pass >= 2 ? 1 : 0;
   const int ps = pass & 1;
   k_cgs_dot<ST><<<dim3((ncol + 7) / 8, maxnrb, nprob), 256, 0, s>>>(dprobs, ph, newvec);
@@ -411,6 +413,7 @@ void launch_step_cgs(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t 
 template <typename ST>
 void launch_step_normalize(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t maxNpad,
                            int start, cudaStream_t s) {
+  count_launch(3);
   // start: 0 regular step, 1 fresh (first or replacement) vector
   k_norm_partial<ST><<<dim3(maxnrb, nprob), 256, 0, s>>>(dprobs, ph, start);
   k_normalize<ST><<<dim3((unsigned)((maxNpad + 255) / 256), nprob), 256, 0, s>>>(dprobs, ph, start);
@@ -420,6 +423,7 @@ void launch_step_normalize(const Prob* dprobs, int nprob, int ph, int maxnrb, in
 template <typename ST>
 void launch_start_vector(const Prob* dprobs, int nprob, int64_t maxNpad, uint64_t seed, const void* v0,
                          cudaStream_t s) {
+  count_launch();
   // fills w for every problem that needs a fresh vector
   k_start_fill<ST><<<dim3((unsigned)((maxNpad + 255) / 256), nprob), 256, 0, s>>>(
       dprobs, seed, (const ST*)v0);
@@ -427,6 +431,7 @@ void launch_start_vector(const Prob* dprobs, int nprob, int64_t maxNpad, uint64_
 
 template <typename ST>
 void launch_restart(const Prob* dprobs, int nprob, int ph, int64_t maxNpad, int ncv, cudaStream_t s) {
+  count_launch(ph ? 5 : 3);
   const unsigned gx = (unsigned)((maxNpad + 63) / 64);
   k_restart_gemm<ST><<<dim3(gx, (ncv + 15) / 16, nprob), 256, 0, s>>>(dprobs, 0);
   if (ph) k_restart_gemm<ST><<<dim3(gx, (ncv + 15) / 16, nprob), 256, 0, s>>>(dprobs, 1);

@@ -273,22 +273,26 @@ template <typename ST>
 void launch_recover(const Prob* dprobs, int iprob, int ph, int64_t Npad, int64_t N, int nev, double2* Z,
                     int ldz, cudaStream_t s) {
   (void)N;
+  count_launch();
   k_recover<ST><<<dim3((unsigned)((Npad + 255) / 256), nev), 256, 0, s>>>(dprobs, iprob, ph, Z, ldz);
 }
 
 void launch_colnormalize(double2* Z, int64_t ldz, int64_t Npad, int k, int ph, double* part, int nrb,
                          cudaStream_t s) {
+  count_launch(2);
   k_colnorm_partial<<<dim3(nrb, k), 256, 0, s>>>(Z, ldz, Npad, ph, part, nrb);
   k_colscale<<<dim3((unsigned)((Npad + 255) / 256), k), 256, 0, s>>>(Z, ldz, Npad, ph, part, nrb);
 }
 
 void launch_prepare_hz2(const double2* Z, int64_t ldz, int64_t Npad, int k, double2* XA, double2* XB,
                         cudaStream_t s) {
+  count_launch();
   k_prepare_hz<<<dim3((unsigned)((Npad + 255) / 256), k), 256, 0, s>>>(Z, ldz, Npad, k, XA, XB);
 }
 
 void launch_residuals2(const double2* Z, int64_t ldz, const double2* U, int64_t Npad, int k, int ph,
                        D4* part, int nrb, double* rho, double* znorm2, double* res, cudaStream_t s) {
+  count_launch(4);
   k_resid_partial<<<dim3(nrb, k), 256, 0, s>>>(Z, ldz, U, Npad, k, ph, rho, part, nrb, 0);
   k_resid_final<<<(k + 127) / 128, 128, 0, s>>>(part, nrb, k, 0, rho, znorm2, res);
   k_resid_partial<<<dim3(nrb, k), 256, 0, s>>>(Z, ldz, U, Npad, k, ph, rho, part, nrb, 1);
@@ -298,12 +302,14 @@ void launch_residuals2(const double2* Z, int64_t ldz, const double2* U, int64_t 
 template <typename ST>
 void launch_store_vectors2(const double2* Z, int64_t ldz, int64_t Npad, int64_t N, int ph, int k,
                            const int* perm, ST* out, int64_t ldo, cudaStream_t s) {
+  count_launch();
   k_store_vectors<ST><<<dim3((unsigned)((N + 255) / 256), k), 256, 0, s>>>(Z, ldz, Npad, N, ph, perm, out, ldo);
 }
 
 template <typename ST, typename R>
 void launch_adjoint2(const double2* Z, int64_t ldz, int64_t Npad, int64_t N, int k, const double* g, int ph,
                      const int2* tiles, int64_t ntiles, ST* dA, ST* dB, cudaStream_t s) {
+  count_launch();
   k_adjoint<ST, R><<<(unsigned)ntiles, 256, 0, s>>>(Z, ldz, Npad, N, k, g, ph, tiles, dA, dB);
 }
 

@@ -303,6 +303,7 @@ k_pack_row(const TIn* __restrict__ rows, int64_t N, int nT, int I, int herm, TSt
 
 template <typename TIn, typename TSt>
 void launch_pack_row(const TIn* rows, int64_t N, int nT, int I, int herm, TSt* dst, cudaStream_t s) {
+  count_launch();
   k_pack_row<TIn, TSt><<<nT - I, 256, 0, s>>>(rows, N, nT, I, herm, dst);
 }
 
@@ -324,6 +325,7 @@ static int num_sms() {
 template <typename ST, typename R>
 void launch_product(const Prob* dprobs, const TileJob* jobs, int njobs, int nprob, int maxnT,
                     int mode, int K, const GenericIO* io_host, bool hasB, cudaStream_t s) {
+  count_launch(2);
   GenericIO io{};
   if (io_host) io = *io_host;
   (void)K;
@@ -346,6 +348,7 @@ template <typename ST, typename R>
 void launch_rowblock(const Prob* dprobs, int prob, int nT, const void* xa, const void* xb, int ldx,
                      double sB, void* y, int ldy, int K, bool hasB, cudaStream_t s) {
   using CT = typename Acc<R>::T;
+  count_launch();
   const size_t sm = (size_t)(2 * RB_Q * TS + 2 * RB_Q * 16) * sizeof(CT);
   dim3 grid(nT, (K + 15) / 16);
   if (hasB) {

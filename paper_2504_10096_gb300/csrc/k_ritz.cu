@@ -319,9 +319,11 @@ __global__ void k_lock_decide(const Prob* __restrict__ probs, int nprob, int ph)
   st->r_k0 = k;
   st->r_nl = nl;
   st->r_nkeep = nkeep;
+  st->r_go = 1;
 }
 
 void launch_ritz(const Prob* dprobs, int nprob, int ncv, cudaStream_t s) {
+  count_launch(2);
   k_ritz_values<<<dim3(ncv, nprob), 32, 0, s>>>(dprobs);
   const size_t sm = (size_t)ncv * 6 * sizeof(double) + (size_t)ncv + 16;
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_ritz_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -329,10 +331,12 @@ void launch_ritz(const Prob* dprobs, int nprob, int ncv, cudaStream_t s) {
 }
 
 void launch_lock_decide(const Prob* dprobs, int nprob, cudaStream_t s) {
+  count_launch();
   k_lock_decide<<<(nprob + 127) / 128, 128, 0, s>>>(dprobs, nprob, 1);
 }
 
 void launch_lock_decide_form(const Prob* dprobs, int nprob, int ph, cudaStream_t s) {
+  count_launch();
   k_lock_decide<<<(nprob + 127) / 128, 128, 0, s>>>(dprobs, nprob, ph);
 }
 

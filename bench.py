@@ -303,13 +303,13 @@ def run_product(args):
     tile kernel of the Lanczos steps, timed with CUDA events on its stream."""
     import torch
     from paper_2504_10096_gb300 import bse
-    from synthetic import BSEProblemSpec, make_problem_torch
+    from synthetic import BSEProblemSpec, make_problem
     torch.cuda.set_device(0)
     N = args.n
     spec = BSEProblemSpec(n=N, n_g=400, seed=1, form="ph", dtype=args.dtype)
-    prob = make_problem_torch(spec, device="cuda")
+    prob = make_problem(spec)          # host generation: no torch.linalg on the device
     stream = torch.cuda.current_stream()
-    s = bse.Solver(prob["A"], prob["B"], stream=stream)
+    s = bse.Solver(torch.from_numpy(prob["A"]).cuda(), torch.from_numpy(prob["B"]).cuda(), stream=stream)
     del prob
     cdt = torch.complex128 if args.dtype == "c128" else torch.complex64
     x = torch.randn(N, dtype=cdt, device="cuda")

@@ -201,6 +201,38 @@ int bse_backward(bse_handle* h, const double* dL_dlambda, int where, void* dA,
  */
 int bse_apply(bse_handle* h, int op, int k, const void* X, void* Y);
 
+/*
+ * bse_apply_noalloc -- one structured product that allocates no device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot let a library call cudaMalloc -- a process whose device memory is
+ * all reserved up front by its own pool allocator, or a latency-bound loop in
+ * which a cudaMalloc (it may synchronise the device) is not acceptable.  It
+ * needs no handle and reads the caller's matrices directly:
+ *
+ *   y = A x                (op BSE_OP_A)
+ *   y = A x + B conj(x)    (op BSE_OP_MPLUS)
+ *   y = A x - B conj(x)    (op BSE_OP_MMINUS)
+ *
+ *   N       1 <= N <= BSE_NOALLOC_MAX_N (4096); larger N returns BSE_EINVAL
+ *   A, B    device, full N x N row-major, complex64 (BSE_C64 / BSE_C64_MIXED)
+ *           or complex128 (BSE_C128); only the upper triangles are read
+ *           (A Hermitian, B symmetric); B may be NULL for BSE_OP_A
+ *   x, y    device, N complex entries each, same dtype; must not overlap
+ *   stream  cudaStream_t (NULL = legacy default stream); the call is
+ *           asynchronous on it
+ *
+ * Its only scratch is a fixed 2 MiB array in the library's device image
+ * (every GPU that loads the library holds it until the process exits).  The
+ * first call on a device looks up that array's address with the device
+ * current; make that first call before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU (other streams or threads) race.
+ * Returns BSE_EINVAL for bad arguments, BSE_ECUDA if a launch fails.
+ */
+#define BSE_NOALLOC_MAX_N 4096
+int bse_apply_noalloc(int64_t N, const void* A, const void* B, int dtype, int op,
+                      const void* x, void* y, void* stream);
+
 /* Counters of the last solve (single-problem handles; for batched handles
    the sums over problems). */
 int bse_get_stats(const bse_handle* h, bse_stats* out);

@@ -26,7 +26,9 @@ BSE_LOWEST = 0
 BSE_OP_A, BSE_OP_MPLUS, BSE_OP_MMINUS, BSE_OP_H = 0, 1, 2, 3
 
 EXPORTED = ["bse_strerror", "bse_create", "bse_create_batched", "bse_solve", "bse_solve_ex",
-            "bse_solve_batched", "bse_backward", "bse_apply", "bse_get_stats", "bse_destroy"]
+            "bse_solve_batched", "bse_backward", "bse_apply", "bse_get_stats", "bse_destroy",
+            "bse_apply_noalloc"]
+BSE_NOALLOC_MAX_N = 4096
 
 
 class bse_solve_opts(ctypes.Structure):
@@ -76,6 +78,7 @@ def load_library(path: str | None = None):
     lib.bse_apply.argtypes = [H, c_int, c_int, c_vp, c_vp]
     lib.bse_get_stats.argtypes = [H, ctypes.POINTER(bse_stats)]
     lib.bse_destroy.argtypes = [H]
+    lib.bse_apply_noalloc.argtypes = [c_i64, c_vp, c_vp, c_int, c_int, c_vp, c_vp, c_vp]
     for name in EXPORTED:
         if name != "bse_strerror":
             getattr(lib, name).restype = c_int
@@ -141,6 +144,11 @@ def bse_backward(h, g_ptr, where, dA_ptr, dB_ptr):
 
 def bse_apply(h, op, k, X_ptr, Y_ptr):
     return load_library().bse_apply(h, op, k, X_ptr, Y_ptr)
+
+
+def bse_apply_noalloc(N, A_ptr, B_ptr, dtype, op, x_ptr, y_ptr, stream=0):
+    """Allocation-free product from full device matrices (N <= BSE_NOALLOC_MAX_N)."""
+    return load_library().bse_apply_noalloc(int(N), A_ptr, B_ptr, dtype, op, x_ptr, y_ptr, stream)
 
 
 def bse_get_stats(h) -> dict:

@@ -199,7 +199,7 @@ def run_gpu(args):
     N = spec.n
 
     def one_step():
-        s = bse.Solver(A, B, stream=stream)
+        s = bse.Solver(A, B, stream=stream, df=args.df)
         vals, vecs, nconv = s.solve(NEV, tol=TOL)
         st = s.stats()
         s.close()
@@ -266,23 +266,44 @@ def run_gpu(args):
     # ---- parity against the stored oracle values
     gold_path = os.path.join(ROOT, "tests", "golden", "config1_omega.txt")
     max_rel = None
+    gold = None
     if os.path.exists(gold_path):
         gold = np.loadtxt(gold_path)
         max_rel = float(np.max(np.abs(vals - gold) / gold))
+    # ---- the same solve with the Lanczos products in double-FP32 (BSE_C128_DF)
+    variant = None
+    if not args.df:
+        s = bse.Solver(A, B, stream=stream, df=True)
+        vdf, _, _, t_df = _timed_solve(s, NEV, TOL, stream, vectors=False)
+        sd = s.stats()
+        s.close()
+        variant = {"dtype": "f64 storage/basis, products in double-FP32 (error-free transformations)",
+                   "s_per_solve": t_df, "krylov_steps": sd["steps"], "max_residual": sd["max_residual"],
+                   "product_GBs": per_launch_bytes / (sd["ms_product"] / sd["passes"] * 1e-3) / 1e9,
+                   "max_rel_err_vs_oracle": float(np.max(np.abs(vdf - gold) / gold)) if gold is not None else None}
     if rank != 0:
         return
     cpu_v, cpu_raw = cpu_baseline_sample()
     value = ms_max / 1e3
+    if args.df:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": achieved_gbs / peaks.get("hbm_gbs", 6800.0), "traffic": None,
+                "kernel": "k_prod_tiles_df + k_prod_reduce (one folded product, double-FP32 arithmetic on "
+                          "split complex128 tiles, 16 B per element)",
+                "peak_kind": peak_kind, "achieved_fp64_equiv_tflops": achieved_tf}
+    else:
+        roof = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved_tf / fp64_peak, "traffic": None,
+                "kernel": "k_prod_tiles + k_prod_reduce (one folded product M+/M- over packed A and B)",
+                "peak_note": "FP64 FMA peak from 152 SMs x 2 FP64 FMA/clk/SM x 2 flops x median SM clock",
+                "achieved_hbm_gbs": achieved_gbs, "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                "hbm_frac": achieved_gbs / peaks.get("hbm_gbs", 6800.0), "hbm_peak_kind": peak_kind}
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(),
-        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved_tf / fp64_peak, "traffic": None,
-                     "kernel": "k_prod_tiles + k_prod_reduce (one folded product M+/M- over packed A and B)",
-                     "peak_note": "FP64 FMA peak from 152 SMs x 2 FP64 FMA/clk/SM x 2 flops x median SM clock",
-                     "achieved_hbm_gbs": achieved_gbs, "hbm_peak_gbs": peaks.get("hbm_gbs"),
-                     "hbm_frac": achieved_gbs / peaks.get("hbm_gbs", 6800.0), "hbm_peak_kind": peak_kind},
+        "vs_baseline": None, "dtype": "f64 (products in double-FP32)" if args.df else "f64",
+        "data": "synthetic", "config": _config(),
+        "roofline": roof,
         "cpu_baseline": {"value": cpu_v, "unit": "s", "cores": _cores(), "kind": "oracle",
                          "sample": f"oracle.ph_lowest (dense zgeev, order {2 * SAMPLE_N}) at N={SAMPLE_N} on the "
                                    f"same recipe, {cpu_raw:.1f} s, scaled by (10000/{SAMPLE_N})^3"},
@@ -294,6 +315,7 @@ def run_gpu(args):
                    "max_residual": stats[-1]["max_residual"], "max_rel_err_vs_oracle": max_rel,
                    "product_ms_per_solve": prod_ms, "product_share": prod_ms / ms},
         "adjoint_ms": adj_ms,
+        "variant_df_products": variant,
     }
     print(json.dumps(line), flush=True)
 
@@ -309,29 +331,161 @@ def run_product(args):
     spec = BSEProblemSpec(n=N, n_g=400, seed=1, form="ph", dtype=args.dtype)
     prob = make_problem(spec)          # host generation: no torch.linalg on the device
     stream = torch.cuda.current_stream()
-    s = bse.Solver(torch.from_numpy(prob["A"]).cuda(), torch.from_numpy(prob["B"]).cuda(), stream=stream)
+    s = bse.Solver(torch.from_numpy(prob["A"]).cuda(), torch.from_numpy(prob["B"]).cuda(), stream=stream,
+                   df=args.df)
     del prob
     cdt = torch.complex128 if args.dtype == "c128" else torch.complex64
     x = torch.randn(N, dtype=cdt, device="cuda")
+    op = bse.BSE_OP_A if args.op == "a" else bse.BSE_OP_MPLUS
     for _ in range(args.warmup):
-        s.apply(bse.BSE_OP_MPLUS, x)
+        s.apply(op, x)
     times = []
-    for _ in range(args.steps):
+    for _ in range(max(args.steps, 10)):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        s.apply(bse.BSE_OP_MPLUS, x)
+        s.apply(op, x)
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     ms = statistics.median(times)
     es = 16 if args.dtype == "c128" else 8
-    byts = 2 * (N * (N + 1) / 2) * es + 3 * N * es
-    flops = 16.0 * N * N
+    nmat = 1 if args.op == "a" else 2
+    byts = nmat * (N * (N + 1) / 2) * es + 3 * N * es
+    flops = 8.0 * nmat * N * N
     peaks, kind = _peaks()
-    print(json.dumps({"mode": "product", "N": N, "dtype": args.dtype, "ms": ms, "GB/s": byts / ms / 1e6,
+    print(json.dumps({"mode": "product", "op": args.op, "N": N, "dtype": args.dtype, "ms": ms, "GB/s": byts / ms / 1e6,
                       "TFLOP/s": flops / ms / 1e9, "hbm_frac": byts / ms / 1e6 / peaks["hbm_gbs"],
                       "hbm_peak_kind": kind}), flush=True)
     s.close()
+
+
+def _timed_solve(solver, nev, tol, stream, vectors=True):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    vals, vecs, nconv = solver.solve(nev, tol=tol, vectors=vectors)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return vals, vecs, nconv, e0.elapsed_time(e1) / 1e3
+
+
+def run_workload(args):
+    """Measurement lines for the other workloads (one JSON line each):
+    tda   -- Tamm-Dancoff, N = 2000, complex128, lowest 20 (FP64)
+    batch -- 64 pseudo-Hermitian problems, N_i ~ U{500..6000}, complex64, 16 each
+    adjoint -- N = 20000, complex64, lowest 50, solve + Hellmann-Feynman backward
+    mixed -- N = 50000, complex64 (mixed path) vs complex128 (FP64 path), lowest 200, tol 1e-6"""
+    import torch
+    from paper_2504_10096_gb300 import bse
+    from synthetic import CONFIGS, batched_specs, loss_draws, make_problem, make_problem_torch
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    out = {"mode": args.mode}
+    if args.mode == "tda":
+        spec = CONFIGS[0]
+        p = make_problem(spec)
+        A = torch.from_numpy(p["A"]).cuda()
+        for _ in range(args.warmup):
+            s = bse.Solver(A, stream=stream); s.solve(spec.nev, tol=1e-12); s.close()
+        ts = []
+        for _ in range(args.steps):
+            s = bse.Solver(A, stream=stream)
+            vals, _, nconv, t = _timed_solve(s, spec.nev, 1e-12, stream)
+            st = s.stats(); s.close(); ts.append(t)
+        gold = np.loadtxt(os.path.join(ROOT, "tests", "golden", "config0_lambda.txt"))
+        out.update({"workload": "TDA N=2000 complex128 nev=20 FP64", "s_per_solve": statistics.median(ts),
+                    "max_rel_err_vs_oracle": float(np.max(np.abs(vals - gold) / np.abs(gold))),
+                    "krylov_steps": st["steps"], "max_residual": st["max_residual"]})
+    elif args.mode == "batch":
+        specs = batched_specs()
+        As, Bs = [], []
+        for sp in specs:
+            p = make_problem(sp)
+            As.append(torch.from_numpy(p["A"]).cuda()); Bs.append(torch.from_numpy(p["B"]).cuda())
+        nev = specs[0].nev
+        ts = []
+        for it in range(args.warmup + args.steps):
+            bs = bse.BatchedSolver(As, Bs, stream=stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(); e0.record(stream)
+            vals, _, nconv = bs.solve(nev, tol=1e-6)
+            e1.record(stream); torch.cuda.synchronize()
+            st = bs.stats(); bs.close()
+            if it >= args.warmup:
+                ts.append(e0.elapsed_time(e1) / 1e3)
+        gold_path = os.path.join(ROOT, "tests", "golden", "config2_omega.txt")
+        err = None
+        if os.path.exists(gold_path):
+            gold = np.loadtxt(gold_path).reshape(len(specs), nev)
+            err = float(np.max(np.abs(vals - gold) / gold))
+        out.update({"workload": "64 PH problems, N_i in [500,6000], complex64, nev=16, tol 1e-6",
+                    "s_per_batch": statistics.median(ts), "sizes_sum": int(sum(s.n for s in specs)),
+                    "max_rel_err_vs_oracle": err, "krylov_steps_total": st["steps"],
+                    "passes_total": st["passes"], "launches": st["launches"], "max_residual": st["max_residual"]})
+    elif args.mode == "adjoint":
+        spec = CONFIGS[3]
+        p = make_problem_torch(spec, device="cuda")
+        A, B = p["A"], p["B"]
+        nev = spec.nev
+        s = bse.Solver(A, B, stream=stream)
+        vals, _, _, t_solve = _timed_solve(s, nev, 1e-6, stream, vectors=False)
+        # FP64 GPU reference on the same complex64 values (targets and gradient reference)
+        s64 = bse.Solver(A.to(torch.complex128), B.to(torch.complex128), stream=stream)
+        ref, _, _, t_ref = _timed_solve(s64, nev, 1e-12, stream, vectors=False)
+        w, noise = loss_draws(nev)
+        targets = ref + noise
+        g = w + 2.0 * (vals - targets)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dA, dB = s.backward(g)
+        e1.record(stream); torch.cuda.synchronize()
+        t_bwd = e0.elapsed_time(e1) / 1e3
+        dA64, dB64 = s64.backward(w + 2.0 * (ref - targets))
+        ra = float(torch.linalg.norm((dA.to(torch.complex128) - dA64)) / torch.linalg.norm(dA64))
+        rb = float(torch.linalg.norm((dB.to(torch.complex128) - dB64)) / torch.linalg.norm(dB64))
+        out.update({"workload": "PH N=20000 complex64 nev=50, loss sum w*l + sum (l-t)^2",
+                    "solve_s": t_solve, "backward_s": t_bwd, "fp64_solve_s": t_ref,
+                    "max_rel_eig_err_vs_fp64_gpu": float(np.max(np.abs(vals - ref) / ref)),
+                    "grad_rel_err_A_vs_fp64_gpu": ra, "grad_rel_err_B_vs_fp64_gpu": rb,
+                    "adjoint_write_GBs": 2 * spec.n ** 2 * 8 / t_bwd / 1e9})
+        s.close(); s64.close()
+    elif args.mode == "mixed":
+        spec = CONFIGS[4]
+        p = make_problem_torch(spec, device="cuda")
+        A, B = p["A"], p["B"]
+        del p
+        nev = spec.nev
+        n = args.n if args.n != 8000 else spec.n     # --n shrinks the workload for trial runs
+        if n != spec.n:
+            A, B = A[:n, :n].contiguous(), B[:n, :n].contiguous()
+        out["N"] = n
+
+        def leg(name, solver):
+            vals, _, nconv, t = _timed_solve(solver, nev, 1e-6, stream, vectors=False)
+            st = solver.stats()
+            solver.close()
+            out.update({f"{name}_s": t, f"{name}_steps": st["steps"], f"{name}_passes": st["passes"],
+                        f"{name}_max_residual": st["max_residual"], f"{name}_nconv": int(nconv),
+                        f"{name}_product_ms_per_pass": st["ms_product"] / max(st["passes"], 1)})
+            return vals, t
+
+        # the mixed path: complex64 storage, FP64 basis, double-FP32 products
+        vals, t_mixed = leg("mixed", bse.Solver(A, B, stream=stream, mixed=True))
+        if args.fp32:    # complex64 with plain FP32 products and basis (residual floor ~eps32 * kappa)
+            v32, _ = leg("fp32", bse.Solver(A, B, stream=stream))
+            out["max_rel_diff_fp32_vs_mixed"] = float(np.max(np.abs(v32 - vals) / vals))
+        if args.fp64 or args.df:
+            A64 = A.to(torch.complex128); del A
+            B64 = B.to(torch.complex128); del B
+            if args.df:
+                vdf, tdf = leg("fp64df", bse.Solver(A64, B64, stream=stream, df=True))
+                out["speedup_mixed_over_fp64df"] = tdf / t_mixed
+            if args.fp64:
+                v64, t64 = leg("fp64", bse.Solver(A64, B64, stream=stream))
+                out["max_rel_diff_mixed_vs_fp64"] = float(np.max(np.abs(vals - v64) / v64))
+                out["speedup_mixed_over_fp64"] = t64 / t_mixed
+    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -340,9 +494,14 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--mode", default="solve", choices=["solve", "product"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "product", "tda", "batch", "adjoint", "mixed"])
     ap.add_argument("--n", type=int, default=8000)
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
+    ap.add_argument("--op", default="mplus", choices=["mplus", "a"])
+    ap.add_argument("--fp64", action="store_true", help="mixed mode: also run the FP64 path")
+    ap.add_argument("--df", action="store_true",
+                    help="complex128 with the Lanczos products in double-FP32 arithmetic (BSE_C128_DF)")
+    ap.add_argument("--fp32", action="store_true", help="mixed mode: also run plain FP32 (BSE_C64)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -350,8 +509,10 @@ def main():
         run_reference(args)
     elif args.mode == "product":
         run_product(args)
-    else:
+    elif args.mode == "solve":
         run_gpu(args)
+    else:
+        run_workload(args)
 
 
 if __name__ == "__main__":

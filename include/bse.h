@@ -64,8 +64,19 @@ typedef enum bse_dtype {
   BSE_C64 = 0,
   /* complex128 storage; FP64 products (the FP64 path) */
   BSE_C128 = 1,
-  /* alias of BSE_C64, kept for the survey's naming of the mixed path */
-  BSE_C64_MIXED = 2
+  /* complex64 input and storage of A and B (half the bytes of BSE_C128);
+     FP64 Krylov basis; the Lanczos products in double-FP32 arithmetic on
+     the complex64 tiles (each stored value is exact in FP32), so the
+     folded iteration is not limited by FP32 rounding; FP64 projected
+     problem, residuals and Rayleigh quotients.  Eigenvectors are returned
+     as complex64. */
+  BSE_C64_MIXED = 2,
+  /* complex128 input and storage, FP64 Krylov basis, projected problem and
+     final residuals; the streaming Lanczos products in double-FP32
+     arithmetic (error-free transformations on the FP32 pipes, 2^-48
+     relative per term) on a split copy of the packed tiles.  Needs twice
+     the packed storage of BSE_C128. */
+  BSE_C128_DF = 3
 } bse_dtype;
 
 typedef enum bse_where { BSE_HOST = 0, BSE_DEVICE = 1 } bse_where;

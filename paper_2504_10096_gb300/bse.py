@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libbse.so")
 BSE_OK, BSE_EINVAL, BSE_ENOMEM, BSE_ENOTPD, BSE_ENOCONV, BSE_ETIMEOUT, BSE_ECUDA, BSE_ESTATE, \
     BSE_ENOTFINITE = range(9)
 BSE_TDA, BSE_PH = 0, 1
-BSE_C64, BSE_C128, BSE_C64_MIXED = 0, 1, 2
+BSE_C64, BSE_C128, BSE_C64_MIXED, BSE_C128_DF = 0, 1, 2, 3
 BSE_HOST, BSE_DEVICE = 0, 1
 BSE_LOWEST = 0
 BSE_OP_A, BSE_OP_MPLUS, BSE_OP_MMINUS, BSE_OP_H = 0, 1, 2, 3
@@ -185,7 +185,11 @@ class Solver:
     device or numpy arrays on the host.  Only their upper triangles are read.
     """
 
-    def __init__(self, A, B=None, form=None, stream=None):
+    def __init__(self, A, B=None, form=None, stream=None, df=False, mixed=False):
+        """df=True (complex128 input only): Lanczos products in double-FP32
+        arithmetic (dtype BSE_C128_DF); everything else stays FP64.
+        mixed=True (complex64 input only): dtype BSE_C64_MIXED (complex64
+        storage, FP64 basis, double-FP32 products)."""
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("libbse needs a CUDA device")
@@ -217,6 +221,14 @@ class Solver:
                 self.device = A.device
         self.N = int(A.shape[0])
         self.cdtype = torch.complex128 if self.dtype == BSE_C128 else torch.complex64
+        if df:
+            if self.dtype != BSE_C128:
+                raise TypeError("df products need complex128 A and B")
+            self.dtype = BSE_C128_DF
+        if mixed:
+            if self.dtype != BSE_C64:
+                raise TypeError("the mixed path needs complex64 A and B")
+            self.dtype = BSE_C64_MIXED
         with torch.cuda.device(self.device):
             self.h = bse_create(self.N, aptr, bptr, self.form, self.dtype, where, self.stream.cuda_stream)
         self.nev = 0

@@ -25,6 +25,8 @@ struct ProbHost {
   int64_t ntiles = 0;
   void* A = nullptr;
   void* B = nullptr;
+  void* Ahl = nullptr;   // split tiles (BSE_C128_DF)
+  void* Bhl = nullptr;
   // solve buffers
   int ncv = 0;
   void *V = nullptr, *P = nullptr, *V2 = nullptr, *P2 = nullptr, *w = nullptr, *pw = nullptr;
@@ -42,6 +44,10 @@ struct ProbHost {
 
 struct bse_handle {
   int count = 0, form = 0, dtype = 0, ph = 0;
+  bool df = false;       // Lanczos products in double-FP32 arithmetic
+  bool split = false;    // ... on split complex128 tiles (else on complex64 tiles)
+  bool tiles64 = false;  // packed tiles are complex64
+  size_t vs = 0;         // bytes per complex element of the Krylov vectors
   size_t es = 0;  // bytes per stored complex element
   cudaStream_t stream = nullptr;
   std::vector<ProbHost> p;
@@ -165,8 +171,12 @@ struct Driver {
   void product(int mode) {
     const bool timed = h->ev_used + 2 <= (int)h->ev.size();
     if (timed) cudaEventRecord(h->ev[h->ev_used], h->stream);
-    launch_product<ST, R>(h->dprobs, h->djobs, h->njobs, h->count, h->maxnT, mode, 1, nullptr, h->ph != 0,
-                          h->stream);
+    if (h->df)
+      launch_product_df(h->dprobs, h->djobs, h->njobs, h->count, h->maxnT, mode, nullptr, h->ph != 0, h->split,
+                        h->stream);
+    else
+      launch_product<ST, R>(h->dprobs, h->djobs, h->njobs, h->count, h->maxnT, mode, 1, nullptr, h->ph != 0,
+                            h->stream);
     if (timed) {
       cudaEventRecord(h->ev[h->ev_used + 1], h->stream);
       h->ev_used += 2;
@@ -287,14 +297,17 @@ struct Driver {
     double* res = z2 + k;
     launch_recover<ST>(h->dprobs, i, h->ph, Npad, q.N, k, q.Z, (int)ldz, h->stream);
     launch_colnormalize(q.Z, ldz, Npad, k, h->ph, (double*)part4, nrb, h->stream);
-    if (h->ph) {
-      launch_prepare_hz2(q.Z, ldz, Npad, k, XA, XB, h->stream);
-      launch_rowblock<ST, double>(h->dprobs, i, q.nT, XA, XB, (int)Npad, 1.0, U, (int)Npad, kc, true,
-                                  h->stream);
-    } else {
-      launch_rowblock<ST, double>(h->dprobs, i, q.nT, q.Z, nullptr, (int)Npad, 0.0, U, (int)Npad, kc, false,
-                                  h->stream);
-    }
+    // FP64 products with the stored tiles (complex64 or complex128)
+    const void* xa = h->ph ? (const void*)XA : (const void*)q.Z;
+    const void* xb = h->ph ? (const void*)XB : nullptr;
+    const double sgn = h->ph ? 1.0 : 0.0;
+    if (h->ph) launch_prepare_hz2(q.Z, ldz, Npad, k, XA, XB, h->stream);
+    if (h->tiles64)
+      launch_rowblock<float2, double>(h->dprobs, i, q.nT, xa, xb, (int)Npad, sgn, U, (int)Npad, kc, h->ph != 0,
+                                      h->stream);
+    else
+      launch_rowblock<double2, double>(h->dprobs, i, q.nT, xa, xb, (int)Npad, sgn, U, (int)Npad, kc, h->ph != 0,
+                                       h->stream);
     launch_residuals2(q.Z, ldz, U, Npad, k, h->ph, part4, nrb, rho, z2, res, h->stream);
     CK(cudaGetLastError());
     std::vector<double> hr(k), hres(k);
@@ -318,15 +331,19 @@ struct Driver {
     if (!out || q.nconv == 0) return BSE_OK;
     const int64_t ldz = h->ph ? 2 * q.Npad : q.Npad;
     const int64_t ldo = h->ph ? 2 * q.N : q.N;
-    launch_store_vectors2<ST>(q.Z, ldz, q.Npad, q.N, h->ph, q.nconv, q.perm, (ST*)out, ldo, h->stream);
+    if (is_c64(h->dtype))   // caller-facing vectors in the handle's dtype
+      launch_store_vectors2<float2>(q.Z, ldz, q.Npad, q.N, h->ph, q.nconv, q.perm, (float2*)out, ldo, h->stream);
+    else
+      launch_store_vectors2<double2>(q.Z, ldz, q.Npad, q.N, h->ph, q.nconv, q.perm, (double2*)out, ldo,
+                                     h->stream);
     CK(cudaGetLastError());
     return BSE_OK;
   }
 };
 
 int alloc_solve(bse_handle* h, int ncv) {
-  const size_t es = h->es;
-  const size_t cs = es;  // product partials in the storage precision
+  const size_t es = h->vs;  // Krylov vectors
+  const size_t cs = es;     // product partials in the vectors' precision
   for (int i = 0; i < h->count; ++i) {
     ProbHost& q = h->p[i];
     if (q.ncv == ncv) continue;
@@ -380,6 +397,8 @@ int upload_probs(bse_handle* h) {
     d.S = q.S;
     d.nrb = nrb_of(q.Npad);
     d.st = h->dstate + i;
+    d.Ahl = q.Ahl;
+    d.Bhl = q.Bhl;
   }
   CK(cudaMemcpyAsync(h->dprobs, h->hprobs.data(), sizeof(Prob) * h->count, cudaMemcpyHostToDevice,
                      h->stream));
@@ -552,8 +571,12 @@ int apply_impl(bse_handle* h, int op, int k, const void* X, void* Y) {
     io.xa = q.w;
     io.y = q.pw;
     io.sB = op == BSE_OP_A ? 0.0 : (op == BSE_OP_MPLUS ? 1.0 : -1.0);
-    launch_product<ST, R>(h->dprobs, h->djobs, h->njobs, 1, h->maxnT, PM_GENERIC, 1, &io,
-                          hasB && op != BSE_OP_A, h->stream);
+    if (h->df && h->split)   // complex128 handle: the solver's double-FP32 product
+      launch_product_df(h->dprobs, h->djobs, h->njobs, 1, h->maxnT, PM_GENERIC, &io, hasB && op != BSE_OP_A,
+                        true, h->stream);
+    else
+      launch_product<ST, R>(h->dprobs, h->djobs, h->njobs, 1, h->maxnT, PM_GENERIC, 1, &io,
+                            hasB && op != BSE_OP_A, h->stream);
     CK(cudaMemcpyAsync(Y, q.pw, h->es * (size_t)N, cudaMemcpyDeviceToDevice, h->stream));
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
@@ -660,7 +683,8 @@ int bse_create_batched(int count, const int64_t* N, const void* const* A, const 
   *out = nullptr;
   if (count < 1 || !N || !A) return BSE_EINVAL;
   if (form != BSE_TDA && form != BSE_PH) return BSE_EINVAL;
-  if (dtype != BSE_C64 && dtype != BSE_C128 && dtype != BSE_C64_MIXED) return BSE_EINVAL;
+  if (dtype != BSE_C64 && dtype != BSE_C128 && dtype != BSE_C64_MIXED && dtype != BSE_C128_DF)
+    return BSE_EINVAL;
   if (where != BSE_HOST && where != BSE_DEVICE) return BSE_EINVAL;
   for (int i = 0; i < count; ++i) {
     if (N[i] < 1 || N[i] > 2147483647LL || !A[i]) return BSE_EINVAL;
@@ -672,7 +696,11 @@ int bse_create_batched(int count, const int64_t* N, const void* const* A, const 
   h->form = form;
   h->dtype = dtype;
   h->ph = form == BSE_PH;
-  h->es = is_c64(dtype) ? sizeof(float2) : sizeof(double2);
+  h->df = dtype == BSE_C128_DF || dtype == BSE_C64_MIXED;
+  h->split = dtype == BSE_C128_DF;
+  h->tiles64 = is_c64(dtype);
+  h->es = is_c64(dtype) ? sizeof(float2) : sizeof(double2);   // stored (tile / caller) elements
+  h->vs = dtype == BSE_C64 ? sizeof(float2) : sizeof(double2);  // Krylov vectors
   h->stream = (cudaStream_t)stream;
   h->p.resize(count);
   h->hstate.resize(count);
@@ -696,6 +724,13 @@ int bse_create_batched(int count, const int64_t* N, const void* const* A, const 
     } else {
       rc = pack_matrix<double2>(h, (const double2*)A[i], q.N, q.nT, 1, where, (double2*)q.A);
       if (!rc && h->ph) rc = pack_matrix<double2>(h, (const double2*)B[i], q.N, q.nT, 0, where, (double2*)q.B);
+      if (!rc && h->df) {
+        const int64_t nel = q.ntiles * TS * TS;
+        if (!(rc = dalloc(&q.Ahl, sizeof(float4) * (size_t)nel)))
+          launch_split_tiles((const double2*)q.A, nel, (float4*)q.Ahl, h->stream);
+        if (!rc && h->ph && !(rc = dalloc(&q.Bhl, sizeof(float4) * (size_t)nel)))
+          launch_split_tiles((const double2*)q.B, nel, (float4*)q.Bhl, h->stream);
+      }
     }
     for (int I = 0; I < q.nT; ++I)
       for (int J = I; J < q.nT; ++J) {
@@ -738,7 +773,7 @@ int bse_solve_ex(bse_handle* h, int nev, double tol, int which, const bse_solve_
   if (!h || which != BSE_LOWEST) return BSE_EINVAL;
   if (h->count != 1) return BSE_EINVAL;
   void* const ev[1] = {evec_out};
-  if (is_c64(h->dtype)) return solve_impl<float2>(h, nev, tol, opts, eval_out, ev, nconv_out);
+  if (h->vs == sizeof(float2)) return solve_impl<float2>(h, nev, tol, opts, eval_out, ev, nconv_out);
   return solve_impl<double2>(h, nev, tol, opts, eval_out, ev, nconv_out);
 }
 
@@ -749,7 +784,7 @@ int bse_solve(bse_handle* h, int nev, double tol, int which, double* eval_out, v
 int bse_solve_batched(bse_handle* h, int nev, double tol, int which, const bse_solve_opts* opts,
                       double* eval_out, void* const* evec_out, int* nconv_out) {
   if (!h || which != BSE_LOWEST) return BSE_EINVAL;
-  if (is_c64(h->dtype)) return solve_impl<float2>(h, nev, tol, opts, eval_out, evec_out, nconv_out);
+  if (h->vs == sizeof(float2)) return solve_impl<float2>(h, nev, tol, opts, eval_out, evec_out, nconv_out);
   return solve_impl<double2>(h, nev, tol, opts, eval_out, evec_out, nconv_out);
 }
 
@@ -785,6 +820,8 @@ int bse_destroy(bse_handle* h) {
     free_results(q);
     dfree(q.A);
     dfree(q.B);
+    dfree(q.Ahl);
+    dfree(q.Bhl);
   }
   dfreet(h->dprobs);
   dfreet(h->dstate);

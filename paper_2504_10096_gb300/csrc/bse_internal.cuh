@@ -115,6 +115,10 @@ struct Prob {
   double* S;          // ncv x ncv, column-major, ld ncv
   int nrb;            // row blocks of the tall-skinny reductions
   KState* st;
+  // complex128 path with double-FP32 products: the packed tiles split into
+  // (hi, lo) float pairs, float4 {re_hi, im_hi, re_lo, im_lo} per element
+  const void* Ahl;
+  const void* Bhl;
 };
 
 // Jobs of the tiled product: problem, tile row I, tile column J, tile index.
@@ -155,6 +159,12 @@ void launch_product(const Prob* dprobs, const TileJob* jobs, int njobs, int npro
 template <typename ST, typename R>
 void launch_rowblock(const Prob* dprobs, int prob, int nT, const void* xa, const void* xb, int ldx,
                      double sB, void* y, int ldy, int K, bool hasB, cudaStream_t s);
+// complex128 products in double-FP32 arithmetic on the split tiles (k_product.cu)
+// split = true: float4 split complex128 tiles; false: complex64 tiles (exact in FP32)
+void launch_product_df(const Prob* dprobs, const TileJob* jobs, int njobs, int nprob, int maxnT,
+                       int mode, const GenericIO* io_host, bool hasB, bool split, cudaStream_t s);
+void launch_split_tiles(const double2* packed, int64_t nelem, float4* split, cudaStream_t s);
+void launch_prod_reduce_d(const Prob* dprobs, int nprob, int maxnT, int mode, GenericIO io, cudaStream_t s);
 
 // Krylov kernels (k_krylov.cu)
 template <typename ST>

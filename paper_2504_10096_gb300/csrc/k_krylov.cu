@@ -67,7 +67,15 @@ k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec) {
   const int64_t r0 = (int64_t)rb * ROWBLK;
   const int64_t r1 = min((int64_t)p.Npad, r0 + ROWBLK);
   ST acc = czero<ST>();
-  for (int64_t r = r0 + lane; r < r1; r += 32) cfmac(acc, __ldg(Q + r), __ldg(w + r));
+  if (ph) {   // K-inner products are real: Re(conj(q) w) only
+    for (int64_t r = r0 + lane; r < r1; r += 32) {
+      const ST q = __ldg(Q + r), x = __ldg(w + r);
+      acc.x = fma(q.x, x.x, acc.x);
+      acc.x = fma(q.y, x.y, acc.x);
+    }
+  } else {
+    for (int64_t r = r0 + lane; r < r1; r += 32) cfmac(acc, __ldg(Q + r), __ldg(w + r));
+  }
   double2 a = mk((double)acc.x, (double)acc.y);
 #pragma unroll
   for (int m = 16; m >= 1; m >>= 1) a = cadd(a, dshfl(a, m));

@@ -329,7 +329,19 @@ void launch_product(const Prob* dprobs, const TileJob* jobs, int njobs, int npro
   GenericIO io{};
   if (io_host) io = *io_host;
   (void)K;
-  int grid = 2 * num_sms();
+  // one wave: as many CTAs as can be resident at once (registers bound the
+  // FP64 variant to one CTA per SM), each streaming a contiguous run of tiles
+  static int occ[2][2] = {{0, 0}, {0, 0}};
+  const int ib = hasB ? 1 : 0, ir = sizeof(R) == 8 ? 1 : 0;
+  if (!occ[ib][ir]) {
+    int o = 0;
+    if (hasB)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_prod_tiles<ST, R, true>, PROD_THREADS, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_prod_tiles<ST, R, false>, PROD_THREADS, 0);
+    occ[ib][ir] = o > 0 ? o : 1;
+  }
+  int grid = occ[ib][ir] * num_sms();
   if (grid > njobs) grid = njobs;
   if (grid < 1) grid = 1;
   if (hasB)
@@ -337,6 +349,10 @@ void launch_product(const Prob* dprobs, const TileJob* jobs, int njobs, int npro
   else
     k_prod_tiles<ST, R, false><<<grid, PROD_THREADS, 0, s>>>(dprobs, jobs, njobs, mode, io);
   k_prod_reduce<ST, R><<<dim3(maxnT, nprob), 256, 0, s>>>(dprobs, mode, io);
+}
+
+void launch_prod_reduce_d(const Prob* dprobs, int nprob, int maxnT, int mode, GenericIO io, cudaStream_t s) {
+  k_prod_reduce<double2, double><<<dim3(maxnT, nprob), 256, 0, s>>>(dprobs, mode, io);
 }
 
 template void launch_product<double2, double>(const Prob*, const TileJob*, int, int, int, int, int,

@@ -74,3 +74,19 @@ def test_tda_handle_apply():
     with pytest.raises(bse.BSEError):
         s.apply(bse.BSE_OP_MPLUS, torch.from_numpy(X).cuda())
     s.close()
+
+
+@pytest.mark.parametrize("n", [37, 129, 515])
+def test_apply_df64_products(n):
+    """complex128 handle with double-FP32 products (BSE_C128_DF): every op
+    against the FP64 oracle; the per-term error is 2^-48, far below FP32."""
+    from paper_2504_10096_gb300 import bse
+    A, B = problem(n, "c128", seed=n + 3)
+    s = bse.Solver(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), df=True)
+    X = rand_block(n, 1, "c128", seed=5)
+    Xt = torch.from_numpy(X).cuda()
+    for op, ref in ((bse.BSE_OP_A, O.apply_a(A, X)), (bse.BSE_OP_MPLUS, O.apply_mplus(A, B, X)),
+                    (bse.BSE_OP_MMINUS, O.apply_mminus(A, B, X))):
+        Y = s.apply(op, Xt).cpu().numpy()
+        assert rel(Y, ref) < 1e-12, (op, rel(Y, ref))
+    s.close()

@@ -139,3 +139,38 @@ def test_config0_tda_n2000():
     lam, _ = O.tda_lowest(p["A"], spec.nev)
     np.testing.assert_allclose(vals, lam, rtol=1e-10, atol=0)
     s.close()
+
+
+@pytest.mark.parametrize("form", ["ph", "tda"])
+def test_df64_products_solve(form):
+    """BSE_C128_DF reaches the FP64-path tolerances (eigenvalues 1e-10)."""
+    from paper_2504_10096_gb300 import bse
+    n, nev = 515, 12
+    A, B = problem(n, "c128", form=form, seed=77)
+    s = bse.Solver(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda() if form == "ph" else None, df=True)
+    vals, vecs, nconv = s.solve(nev, tol=1e-12)
+    ref = O.ph_lowest(A, B, nev)[0] if form == "ph" else O.tda_lowest(A, nev)[0]
+    assert nconv == nev
+    np.testing.assert_allclose(vals, ref, rtol=1e-10, atol=0)
+    assert s.stats()["max_residual"] < 1e-11
+    s.close()
+
+
+def test_mixed_c64_storage_reaches_fp64_class():
+    """BSE_C64_MIXED: complex64 storage, FP64 basis, double-FP32 products --
+    residuals far below what FP32 products allow (the folded operator
+    squares the spectral range), eigenvalues at the FP64-path tolerance."""
+    from paper_2504_10096_gb300 import bse
+    n, nev = 600, 12
+    A, B = problem(n, "c64", seed=19)
+    s = bse.Solver(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), mixed=True)
+    vals, vecs, nconv = s.solve(nev, tol=1e-10)
+    om, Xo, Yo = O.ph_lowest(A.astype(np.complex128), B.astype(np.complex128), nev)
+    assert nconv == nev
+    np.testing.assert_allclose(vals, om, rtol=1e-10, atol=0)
+    assert s.stats()["max_residual"] < 1e-9
+    Z = vecs.cpu().numpy().astype(np.complex128)
+    assert vecs.dtype == torch.complex64
+    ov = np.abs(np.einsum("ij,ij->j", Z.conj(), omega_metric_apply(np.vstack([Xo, Yo]))))
+    np.testing.assert_allclose(ov, 1.0, atol=1e-6)
+    s.close()

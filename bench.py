@@ -401,8 +401,8 @@ def run_workload(args):
         specs = batched_specs()
         As, Bs = [], []
         for sp in specs:
-            p = make_problem(sp)
-            As.append(torch.from_numpy(p["A"]).cuda()); Bs.append(torch.from_numpy(p["B"]).cuda())
+            p = make_problem_torch(sp, device="cuda")
+            As.append(p["A"]); Bs.append(p["B"])
         nev = specs[0].nev
         ts = []
         for it in range(args.warmup + args.steps):

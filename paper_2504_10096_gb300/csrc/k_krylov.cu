@@ -68,12 +68,16 @@ k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec) {
   const int64_t r1 = min((int64_t)p.Npad, r0 + ROWBLK);
   ST acc = czero<ST>();
   if (ph) {   // K-inner products are real: Re(conj(q) w) only
+    R a1 = 0, a2 = 0;   // two chains (x and y products) for more ILP
+#pragma unroll 8
     for (int64_t r = r0 + lane; r < r1; r += 32) {
       const ST q = __ldg(Q + r), x = __ldg(w + r);
-      acc.x = fma(q.x, x.x, acc.x);
-      acc.x = fma(q.y, x.y, acc.x);
+      a1 = fma(q.x, x.x, a1);
+      a2 = fma(q.y, x.y, a2);
     }
+    acc.x = a1 + a2;
   } else {
+#pragma unroll 8
     for (int64_t r = r0 + lane; r < r1; r += 32) cfmac(acc, __ldg(Q + r), __ldg(w + r));
   }
   double2 a = mk((double)acc.x, (double)acc.y);
@@ -115,19 +119,40 @@ k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= p.Npad) return;
   const ST* V = (const ST*)p.V;
-  ST acc = czero<ST>();
+  // four independent accumulators keep four column loads in flight per thread
+  ST acc[4] = {czero<ST>(), czero<ST>(), czero<ST>(), czero<ST>()};
+  const int nj = j + 1;                     // basis columns [0, j], then the twins
   if (ph) {
-    for (int c = 0; c < nset; ++c) {
-      const ST v = __ldg(V + (int64_t)set_col(c, j, p.ncv) * p.Npad + row);
+    const ST* tw = V + (int64_t)(p.ncv + 1) * p.Npad + row;
+    const ST* vb = V + row;
+    int c = 0;
+    for (; c + 4 <= nset; c += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int cc = c + u;
+        const ST v = __ldg((cc < nj ? vb + (int64_t)cc * p.Npad : tw + (int64_t)(cc - nj) * p.Npad));
+        const R f = cf[cc].x;
+        acc[u].x = fma(v.x, f, acc[u].x);
+        acc[u].y = fma(v.y, f, acc[u].y);
+      }
+    }
+    for (; c < nset; ++c) {
+      const ST v = __ldg((c < nj ? vb + (int64_t)c * p.Npad : tw + (int64_t)(c - nj) * p.Npad));
       const R f = cf[c].x;
-      acc.x = fma(v.x, f, acc.x);
-      acc.y = fma(v.y, f, acc.y);
+      acc[0].x = fma(v.x, f, acc[0].x);
+      acc[0].y = fma(v.y, f, acc[0].y);
     }
   } else {
-    for (int c = 0; c < nset; ++c) cfma(acc, __ldg(V + (int64_t)c * p.Npad + row), cf[c]);
+    int c = 0;
+    for (; c + 4 <= nset; c += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) cfma(acc[u], __ldg(V + (int64_t)(c + u) * p.Npad + row), cf[c + u]);
+    }
+    for (; c < nset; ++c) cfma(acc[0], __ldg(V + (int64_t)c * p.Npad + row), cf[c]);
   }
+  const ST tot = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
   ST* w = (ST*)p.w;
-  w[row] = csub(w[row], acc);
+  w[row] = csub(w[row], tot);
 }
 
 // ---------------------------------------------------------------- norms

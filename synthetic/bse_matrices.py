@@ -191,23 +191,12 @@ def make_problem_torch(spec: BSEProblemSpec, device="cuda"):
     cdt = torch.complex64 if spec.dtype == "c64" else torch.complex128
     vt = torch.from_numpy(v).to(device)
     out = {"energies": energies}
-    # norms in FP64 on the device (N_G x N_G Gram matrices)
-    r = torch.from_numpy(rho).to(device)
-    rw = torch.from_numpy(rho_w).to(device)
-    sq = vt.sqrt()[:, None]
-    f = sq * r
-    fw = sq * rw
-    lam_x = torch.linalg.eigvalsh(f @ f.conj().T)[-1].item()
-    lam_w = torch.linalg.eigvalsh(fw @ fw.conj().T)[-1].item()
-    s_x, s_w = spec.kx_norm / lam_x, spec.w_norm / lam_w
-    s_b = 0.0
-    if spec.form == "ph":
-        r1 = torch.linalg.qr(f.conj().T, mode="r")[1]
-        r2 = torch.linalg.qr(f.T, mode="r")[1]
-        s_b = spec.b_norm / torch.linalg.svdvals(r1 @ r2.conj().T)[0].item()
-    del f, fw
-    rc, rwc, vc = r.to(cdt), rw.to(cdt), vt.to(cdt)
-    del r, rw
+    # scale factors on the host, with the same code as make_problem (the
+    # device only runs plain matrix products)
+    s_x, s_w, s_b = _scales(rho, rho_w, v, spec)
+    rc = torch.from_numpy(rho).to(device=device, dtype=cdt)
+    rwc = torch.from_numpy(rho_w).to(device=device, dtype=cdt)
+    vc = vt.to(cdt)
     a = (s_x * rc.conj().T) @ (vc[:, None] * rc)
     a -= (s_w * rwc.conj().T) @ (vc[:, None] * rwc)
     del rwc

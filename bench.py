@@ -111,7 +111,8 @@ def _reduce_max(x, ws):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -170,14 +171,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _config():
+def _config(ncv=0):
     return {"workload": "pseudo-Hermitian BSE, N=10000 (H 20000x20000), complex128, lowest 100 positive "
                         "eigenpairs, FP64 structure-preserving thick-restart Lanczos, tol 1e-12",
             "N": 10000, "nev": NEV, "tol": TOL, "storage": "complex128", "seed": 1,
+            "ncv": ncv or max(2 * NEV, NEV + 32),
             "l2": "inputs larger than L2 (packed A+B 1.6 GB)", "parallelism": "replicas"}
 
 
 # ------------------------------------------------------------------ GPU arm
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_prod_tiles(+_df) launch at N = 8000
+# (profiles/k_prod_tiles_*_n8000.md); None until the current kernel has been captured
+TRAFFIC_N8000 = {"fp64": 1.057898e9 + 10.356224e6, "df": 1.067138e9 + 22.040064e6}
+
+
 def run_gpu(args):
     import torch
     ws, rank, local = _dist()
@@ -200,7 +207,7 @@ def run_gpu(args):
 
     def one_step():
         s = bse.Solver(A, B, stream=stream, df=args.df)
-        vals, vecs, nconv = s.solve(NEV, tol=TOL)
+        vals, vecs, nconv = s.solve(NEV, tol=TOL, ncv=args.ncv)
         st = s.stats()
         s.close()
         return vals, st
@@ -228,7 +235,9 @@ def run_gpu(args):
     n_tiles = (spec.n + 127) // 128
     launches = int(sum(s["launches"] for s in stats) / args.steps) + 2 * n_tiles  # + packing of A and B
     # ---- block-product roofline (the dominant kernel): FP64 complex products
-    per_launch_flops = 16.0 * N * N                       # A x + B conj(x): 8 flops per complex MAC
+    # M_s as a real-linear map on R^2N is a dense 2N x 2N real matrix: 4N^2 FMAs = 8N^2 flops
+    # (forming A x and B conj(x) as two complex products would be 16N^2)
+    per_launch_flops = 8.0 * N * N
     per_launch_bytes = 2 * (N * (N + 1) / 2) * 16 + 3 * N * 16
     t_launch = prod_ms / passes * 1e-3
     peaks, peak_kind = _peaks()
@@ -285,15 +294,22 @@ def run_gpu(args):
         return
     cpu_v, cpu_raw = cpu_baseline_sample()
     value = ms_max / 1e3
+    # DRAM traffic per launch from the ncu captures at N = 8000 (profiles/k_prod_tiles_c128_n8000.md,
+    # profiles/k_prod_tiles_df_n8000.md): bytes per stored 128x128 tile pair, scaled by the tile
+    # count of this workload (traffic grows with the number of tiles streamed)
+    n_tiles_8000 = 63 * 64 // 2
+    captured = TRAFFIC_N8000.get("df" if args.df else "fp64")
+    traffic = None if captured is None else captured / (2 * n_tiles_8000) * 2 * (n_tiles * (n_tiles + 1) // 2)
     if args.df:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                "frac": achieved_gbs / peaks.get("hbm_gbs", 6800.0), "traffic": None,
+                "frac": achieved_gbs / peaks.get("hbm_gbs", 6800.0), "traffic": traffic,
                 "kernel": "k_prod_tiles_df + k_prod_reduce (one folded product, double-FP32 arithmetic on "
                           "split complex128 tiles, 16 B per element)",
                 "peak_kind": peak_kind, "achieved_fp64_equiv_tflops": achieved_tf}
     else:
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved_tf / fp64_peak, "traffic": None,
+                "frac": achieved_tf / fp64_peak, "traffic": traffic,
+                "algorithmic_bytes": per_launch_bytes,
                 "kernel": "k_prod_tiles + k_prod_reduce (one folded product M+/M- over packed A and B)",
                 "peak_note": "FP64 FMA peak from 152 SMs x 2 FP64 FMA/clk/SM x 2 flops x median SM clock",
                 "achieved_hbm_gbs": achieved_gbs, "hbm_peak_gbs": peaks.get("hbm_gbs"),
@@ -302,7 +318,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64 (products in double-FP32)" if args.df else "f64",
-        "data": "synthetic", "config": _config(),
+        "data": "synthetic", "config": _config(args.ncv),
         "roofline": roof,
         "cpu_baseline": {"value": cpu_v, "unit": "s", "cores": _cores(), "kind": "oracle",
                          "sample": f"oracle.ph_lowest (dense zgeev, order {2 * SAMPLE_N}) at N={SAMPLE_N} on the "
@@ -313,7 +329,10 @@ def run_gpu(args):
         "clocks": clocks,
         "solver": {"krylov_steps": stats[-1]["steps"], "passes": passes, "restarts": stats[-1]["restarts"],
                    "max_residual": stats[-1]["max_residual"], "max_rel_err_vs_oracle": max_rel,
-                   "product_ms_per_solve": prod_ms, "product_share": prod_ms / ms},
+                   "product_ms_per_solve": prod_ms, "product_share": prod_ms / ms,
+                   "product_shape": {"ctas_per_sm": stats[-1]["shape_ctas_per_sm"],
+                                     "strided": stats[-1]["shape_strided"], "tuned": stats[-1]["tuned"]},
+                   "krylov_steps_as": "cuda graphs"},
         "adjoint_ms": adj_ms,
         "variant_df_products": variant,
     }
@@ -351,7 +370,7 @@ def run_product(args):
     es = 16 if args.dtype == "c128" else 8
     nmat = 1 if args.op == "a" else 2
     byts = nmat * (N * (N + 1) / 2) * es + 3 * N * es
-    flops = 8.0 * nmat * N * N
+    flops = 8.0 * N * N          # A x (complex) or M_s x (real 2N x 2N form): 4N^2 FMAs
     peaks, kind = _peaks()
     print(json.dumps({"mode": "product", "op": args.op, "N": N, "dtype": args.dtype, "ms": ms, "GB/s": byts / ms / 1e6,
                       "TFLOP/s": flops / ms / 1e9, "hbm_frac": byts / ms / 1e6 / peaks["hbm_gbs"],
@@ -359,12 +378,12 @@ def run_product(args):
     s.close()
 
 
-def _timed_solve(solver, nev, tol, stream, vectors=True):
+def _timed_solve(solver, nev, tol, stream, vectors=True, graphs=True):
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    vals, vecs, nconv = solver.solve(nev, tol=tol, vectors=vectors)
+    vals, vecs, nconv = solver.solve(nev, tol=tol, vectors=vectors, graphs=graphs)
     e1.record(stream)
     torch.cuda.synchronize()
     return vals, vecs, nconv, e0.elapsed_time(e1) / 1e3
@@ -375,10 +394,11 @@ def run_workload(args):
     tda   -- Tamm-Dancoff, N = 2000, complex128, lowest 20 (FP64)
     batch -- 64 pseudo-Hermitian problems, N_i ~ U{500..6000}, complex64, 16 each
     adjoint -- N = 20000, complex64, lowest 50, solve + Hellmann-Feynman backward
-    mixed -- N = 50000, complex64 (mixed path) vs complex128 (FP64 path), lowest 200, tol 1e-6"""
+    mixed -- N = 50000, complex64 (mixed path) vs complex128 (FP64 path), lowest 200, tol 1e-6
+    haydock -- N = 10000 pseudo-Hermitian, complex128, Lanczos-Haydock spectrum (600 steps)"""
     import torch
     from paper_2504_10096_gb300 import bse
-    from synthetic import CONFIGS, batched_specs, loss_draws, make_problem, make_problem_torch
+    from synthetic import CONFIGS, batched_specs, loss_draws, make_problem, make_problem_torch, random_start
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     out = {"mode": args.mode}
@@ -388,15 +408,21 @@ def run_workload(args):
         A = torch.from_numpy(p["A"]).cuda()
         for _ in range(args.warmup):
             s = bse.Solver(A, stream=stream); s.solve(spec.nev, tol=1e-12); s.close()
-        ts = []
-        for _ in range(args.steps):
+        ts, ts_stream = [], []
+        for _ in range(max(args.steps, 5)):
             s = bse.Solver(A, stream=stream)
             vals, _, nconv, t = _timed_solve(s, spec.nev, 1e-12, stream)
             st = s.stats(); s.close(); ts.append(t)
+            s = bse.Solver(A, stream=stream)          # the same solve with one launch per kernel
+            _, _, _, t = _timed_solve(s, spec.nev, 1e-12, stream, graphs=False)
+            s.close(); ts_stream.append(t)
         gold = np.loadtxt(os.path.join(ROOT, "tests", "golden", "config0_lambda.txt"))
         out.update({"workload": "TDA N=2000 complex128 nev=20 FP64", "s_per_solve": statistics.median(ts),
+                    "s_per_solve_stream_launches": statistics.median(ts_stream),
                     "max_rel_err_vs_oracle": float(np.max(np.abs(vals - gold) / np.abs(gold))),
-                    "krylov_steps": st["steps"], "max_residual": st["max_residual"]})
+                    "krylov_steps": st["steps"], "max_residual": st["max_residual"], "launches": st["launches"],
+                    "product_shape": {"ctas_per_sm": st["shape_ctas_per_sm"], "strided": st["shape_strided"],
+                                      "tuned": st["tuned"]}})
     elif args.mode == "batch":
         specs = batched_specs()
         As, Bs = [], []
@@ -422,7 +448,9 @@ def run_workload(args):
         out.update({"workload": "64 PH problems, N_i in [500,6000], complex64, nev=16, tol 1e-6",
                     "s_per_batch": statistics.median(ts), "sizes_sum": int(sum(s.n for s in specs)),
                     "max_rel_err_vs_oracle": err, "krylov_steps_total": st["steps"],
-                    "passes_total": st["passes"], "launches": st["launches"], "max_residual": st["max_residual"]})
+                    "passes_total": st["passes"], "launches": st["launches"], "max_residual": st["max_residual"],
+                    "product_shape": {"ctas_per_sm": st["shape_ctas_per_sm"], "strided": st["shape_strided"],
+                                      "tuned": st["tuned"]}})
     elif args.mode == "adjoint":
         spec = CONFIGS[3]
         p = make_problem_torch(spec, device="cuda")
@@ -436,20 +464,61 @@ def run_workload(args):
         w, noise = loss_draws(nev)
         targets = ref + noise
         g = w + 2.0 * (vals - targets)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        dA, dB = s.backward(g)
-        e1.record(stream); torch.cuda.synchronize()
-        t_bwd = e0.elapsed_time(e1) / 1e3
+        def timed_bwd(impl):
+            s.backward(g, impl=impl)                      # warm-up (allocations, tile lists)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = s.backward(g, impl=impl)
+            e1.record(stream); torch.cuda.synchronize()
+            return r, e0.elapsed_time(e1) / 1e3
+        (dA, dB), t_bwd = timed_bwd(bse.BSE_IMPL_TENSOR_CORES)
+        (dAs, dBs), t_simt = timed_bwd(bse.BSE_IMPL_CUDA_CORES)
+        tc_vs_simt = float(torch.linalg.norm(dA - dAs) / torch.linalg.norm(dAs))
+        del dAs, dBs
         dA64, dB64 = s64.backward(w + 2.0 * (ref - targets))
         ra = float(torch.linalg.norm((dA.to(torch.complex128) - dA64)) / torch.linalg.norm(dA64))
         rb = float(torch.linalg.norm((dB.to(torch.complex128) - dB64)) / torch.linalg.norm(dB64))
         out.update({"workload": "PH N=20000 complex64 nev=50, loss sum w*l + sum (l-t)^2",
-                    "solve_s": t_solve, "backward_s": t_bwd, "fp64_solve_s": t_ref,
+                    "solve_s": t_solve, "backward_tc_s": t_bwd, "backward_cuda_cores_s": t_simt,
+                    "tc_vs_cuda_cores_rel_diff": tc_vs_simt, "fp64_solve_s": t_ref,
                     "max_rel_eig_err_vs_fp64_gpu": float(np.max(np.abs(vals - ref) / ref)),
                     "grad_rel_err_A_vs_fp64_gpu": ra, "grad_rel_err_B_vs_fp64_gpu": rb,
-                    "adjoint_write_GBs": 2 * spec.n ** 2 * 8 / t_bwd / 1e9})
+                    "adjoint_write_GBs": 2 * spec.n ** 2 * 8 / t_bwd / 1e9,
+                    "adjoint_write_frac": 2 * spec.n ** 2 * 8 / t_bwd / 1e9 / _peaks()[0]["hbm_gbs"]})
         s.close(); s64.close()
+    elif args.mode == "haydock":
+        # Lanczos-Haydock spectrum on the config-1 shapes (PH, N = 10000, complex128)
+        spec = CONFIGS[1]
+        p = make_problem_torch(spec, device="cuda")
+        A, B = p["A"], p["B"]
+        del p
+        m = 600
+        omega = np.linspace(0.0, 12.0, 4001)
+        d = torch.from_numpy(random_start(spec.n, seed=11)).cuda()
+        ts = []
+        for it in range(args.warmup + args.steps):
+            s = bse.Solver(A, B, stream=stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            spec_v, F, coefs, steps = s.haydock(d, m, omega, 0.05)
+            e1.record(stream); torch.cuda.synchronize()
+            st = s.stats(); s.close()
+            if it >= args.warmup:
+                ts.append(e0.elapsed_time(e1) / 1e3)
+        # oracle recurrence on the host: a bounded sample of steps, scaled to m
+        import oracle as O
+        Ah, Bh = A.cpu().numpy(), B.cpu().numpy()
+        dh = d.cpu().numpy()
+        k = 4
+        t0 = time.perf_counter()
+        O.lanczos_ph(Ah, Bh, dh, k)
+        t_cpu = (time.perf_counter() - t0) / k * m
+        out.update({"workload": f"PH N={spec.n} complex128, Haydock m={m} steps, 4001 frequencies, eta 0.05 eV",
+                    "s_per_spectrum": statistics.median(ts), "steps": steps, "passes": st["passes"],
+                    "ms_per_step": statistics.median(ts) * 1e3 / m, "launches": st["launches"],
+                    "cpu_oracle_s_extrapolated": t_cpu, "cpu_sample": f"{k} oracle steps scaled to {m}",
+                    "cores": os.cpu_count()})
     elif args.mode == "mixed":
         spec = CONFIGS[4]
         p = make_problem_torch(spec, device="cuda")
@@ -494,7 +563,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--mode", default="solve", choices=["solve", "product", "tda", "batch", "adjoint", "mixed"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "product", "tda", "batch", "adjoint", "mixed",
+                                                              "haydock"])
     ap.add_argument("--n", type=int, default=8000)
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
     ap.add_argument("--op", default="mplus", choices=["mplus", "a"])
@@ -502,6 +572,7 @@ def main():
     ap.add_argument("--df", action="store_true",
                     help="complex128 with the Lanczos products in double-FP32 arithmetic (BSE_C128_DF)")
     ap.add_argument("--fp32", action="store_true", help="mixed mode: also run plain FP32 (BSE_C64)")
+    ap.add_argument("--ncv", type=int, default=0, help="solve mode: Krylov subspace size (0 = library default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

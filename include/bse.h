@@ -101,6 +101,10 @@ typedef struct bse_solve_opts {
                          dtype); NULL = counter-based random start            */
   double lock_tol;    /* Ritz-estimate tolerance used for locking, relative
                          to the Ritz value [tol / 4]                          */
+  int stream_launches; /* 0: the Krylov steps of a restart cycle are replayed
+                         as CUDA graphs of 1, 2, 4, ... steps, captured once
+                         per handle and subspace size; nonzero: every kernel
+                         is launched on the stream one by one [0]             */
 } bse_solve_opts;
 
 /* Per-solve counters, filled by bse_get_stats after a solve. */
@@ -113,6 +117,12 @@ typedef struct bse_stats {
   double ms_total;       /* device time of the last solve (CUDA events)       */
   double ms_product;     /* device time inside the structured products        */
   int64_t launches;      /* CUDA kernels launched by the last solve           */
+  int shape_ctas_per_sm; /* launch shape the product tuner chose: CTAs per SM
+                            (0 = as many as fit, -1 = one CTA per tile)       */
+  int shape_strided;     /* 1: each CTA takes every grid-th tile job; 0: a
+                            contiguous run                                    */
+  int tuned;             /* 1 once the shape was chosen by timing (bse_solve
+                            times the candidates on its own first products)   */
 } bse_stats;
 
 /* Human-readable message for a status code (static storage). */
@@ -203,6 +213,21 @@ int bse_solve_batched(bse_handle* h, int nev, double tol, int which,
 int bse_backward(bse_handle* h, const double* dL_dlambda, int where, void* dA,
                  void* dB);
 
+/* Implementation choice for bse_backward_ex. */
+typedef enum bse_impl {
+  BSE_IMPL_AUTO = 0,          /* tensor cores for complex64 outputs, else CUDA cores */
+  BSE_IMPL_CUDA_CORES = 1,    /* SIMT FMA kernel (FP64 for complex128, FP32 for complex64) */
+  BSE_IMPL_TENSOR_CORES = 2   /* tcgen05 3xTF32 rank-2k update; complex64 outputs only */
+} bse_impl;
+
+/* bse_backward with an explicit implementation (impl from bse_impl).  The
+   tensor-core path computes dA, dB as real GEMMs of the stacked eigenvector
+   panels with TF32 hi/lo splits (about FP32 accuracy) and FP32 accumulation
+   in tensor memory; it returns BSE_EINVAL for complex128 handles and
+   BSE_ETIMEOUT if a bounded device-side wait expired. */
+int bse_backward_ex(bse_handle* h, const double* dL_dlambda, int where, void* dA,
+                    void* dB, int impl);
+
 /*
  * bse_apply -- one structured product on device blocks of k columns.
  *   X, Y   device, column-major, handle dtype; N rows (BSE_OP_A/MPLUS/MMINUS)
@@ -244,8 +269,48 @@ int bse_apply(bse_handle* h, int op, int k, const void* X, void* Y);
 int bse_apply_noalloc(int64_t N, const void* A, const void* B, int dtype, int op,
                       const void* x, void* y, void* stream);
 
-/* Counters of the last solve (single-problem handles; for batched handles
-   the sums over problems). */
+/*
+ * bse_haydock -- optical absorption spectrum by the Lanczos-Haydock
+ * recurrence (Sec. 2.2: the iterative route that gives the spectrum from
+ * Lanczos coefficients and continued fractions, without eigenpairs).
+ *
+ * With z = omega + i eta the response is
+ *   TDA: F(z) = d^H (z - A)^{-1} d,
+ *   PH:  F(z) = D^H Omega (z - H)^{-1} D,  D = (d; sign conj(d)),
+ * and spectrum_out[i] = -Im F(omega[i] + i eta) / pi (>= 0 for omega > 0).
+ * TDA runs m steps of the three-term Lanczos recurrence on A from d/|d| and
+ * returns |d|^2 CF(z); PH runs it on the folded operator M+ M- (sign = -1)
+ * or M- M+ (sign = +1), self-adjoint in <x, y> = Re(x^H M-/+ y), and returns
+ * 2 <d, d> CF(z^2), with M+ u = A u + B conj(u), M- w = A w - B conj(w).
+ * There is no re-orthogonalisation: the recurrence is the method, and its
+ * continued fraction converges to F as m grows (for m of order 2N it agrees
+ * with the dense resolvent to rounding).  Each step costs one (TDA) or two
+ * (PH) structured products; the steps replay as a CUDA graph.
+ *
+ *   d             N complex128 values (host or device, per `where`),
+ *                 whatever the handle's dtype
+ *   m             Lanczos steps, 1 <= m <= 10^6 (fewer if the Krylov space
+ *                 becomes invariant: *steps_out says how many)
+ *   sign          -1 or +1 (PH only; ignored for TDA)
+ *   nw, omega     host array of nw >= 1 real frequencies
+ *   eta           broadening, > 0
+ *   spectrum_out  host, nw doubles
+ *   response_out  host, 2 nw doubles (Re F, Im F interleaved) or NULL
+ *   coef_out      host, 2 m + 1 doubles or NULL: alpha_0..alpha_{m-1},
+ *                 beta_0..beta_{m-1} (beta_j couples steps j and j+1; zero
+ *                 beyond *steps_out), then <d, d>
+ *   steps_out     host int or NULL
+ * Single-problem handles only.  The library allocates and frees its own
+ * scratch (6 vectors of N).  BSE_EINVAL for bad arguments, BSE_ENOTPD if
+ * <d, d> (|d|^2, or Re(d^H M-/+ d)) is not positive, BSE_ECUDA on CUDA
+ * errors.  bse_get_stats afterwards reports steps, passes, time, launches.
+ */
+int bse_haydock(bse_handle* h, const void* d, int where, int m, int sign,
+                int nw, const double* omega, double eta, double* spectrum_out,
+                double* response_out, double* coef_out, int* steps_out);
+
+/* Counters of the last solve or spectrum (single-problem handles; for
+   batched handles the sums over problems). */
 int bse_get_stats(const bse_handle* h, bse_stats* out);
 
 /* Release every resource of the handle (synchronises its stream). */

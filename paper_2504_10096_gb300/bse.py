@@ -27,20 +27,23 @@ BSE_OP_A, BSE_OP_MPLUS, BSE_OP_MMINUS, BSE_OP_H = 0, 1, 2, 3
 
 EXPORTED = ["bse_strerror", "bse_create", "bse_create_batched", "bse_solve", "bse_solve_ex",
             "bse_solve_batched", "bse_backward", "bse_apply", "bse_get_stats", "bse_destroy",
-            "bse_apply_noalloc"]
+            "bse_apply_noalloc", "bse_backward_ex", "bse_haydock"]
+BSE_IMPL_AUTO, BSE_IMPL_CUDA_CORES, BSE_IMPL_TENSOR_CORES = 0, 1, 2
 BSE_NOALLOC_MAX_N = 4096
 
 
 class bse_solve_opts(ctypes.Structure):
     _fields_ = [("ncv", ctypes.c_int), ("maxit", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("v0", ctypes.c_void_p), ("lock_tol", ctypes.c_double)]
+                ("v0", ctypes.c_void_p), ("lock_tol", ctypes.c_double),
+                ("stream_launches", ctypes.c_int)]
 
 
 class bse_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("passes", ctypes.c_int64), ("restarts", ctypes.c_int64),
                 ("nconv", ctypes.c_int), ("max_residual", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_product", ctypes.c_double),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("shape_ctas_per_sm", ctypes.c_int),
+                ("shape_strided", ctypes.c_int), ("tuned", ctypes.c_int)]
 
 
 class BSEError(RuntimeError):
@@ -79,6 +82,10 @@ def load_library(path: str | None = None):
     lib.bse_get_stats.argtypes = [H, ctypes.POINTER(bse_stats)]
     lib.bse_destroy.argtypes = [H]
     lib.bse_apply_noalloc.argtypes = [c_i64, c_vp, c_vp, c_int, c_int, c_vp, c_vp, c_vp]
+    lib.bse_backward_ex.argtypes = [H, ctypes.POINTER(c_dbl), c_int, c_vp, c_vp, c_int]
+    PD = ctypes.POINTER(c_dbl)
+    lib.bse_haydock.argtypes = [H, c_vp, c_int, c_int, c_int, c_int, PD, c_dbl, PD, PD, PD,
+                                ctypes.POINTER(c_int)]
     for name in EXPORTED:
         if name != "bse_strerror":
             getattr(lib, name).restype = c_int
@@ -140,6 +147,26 @@ def bse_solve_batched(h, count, nev, tol, which=BSE_LOWEST, opts=None, evec_ptrs
 def bse_backward(h, g_ptr, where, dA_ptr, dB_ptr):
     return load_library().bse_backward(h, ctypes.cast(g_ptr, ctypes.POINTER(ctypes.c_double)), where,
                                        dA_ptr, dB_ptr)
+
+
+def bse_backward_ex(h, g_ptr, where, dA_ptr, dB_ptr, impl=BSE_IMPL_AUTO):
+    return load_library().bse_backward_ex(h, ctypes.cast(g_ptr, ctypes.POINTER(ctypes.c_double)), where,
+                                          dA_ptr, dB_ptr, impl)
+
+
+def bse_haydock(h, d_ptr, where, m, sign, omega, eta, want_coefs=True):
+    """Returns (status, spectrum, response (complex), coefficients, steps)."""
+    omega = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
+    nw = omega.shape[0]
+    spec = np.zeros(nw)
+    resp = np.zeros(2 * nw)
+    coef = np.zeros(2 * m + 1) if want_coefs else None
+    steps = ctypes.c_int(0)
+    P = ctypes.POINTER(ctypes.c_double)
+    rc = load_library().bse_haydock(h, d_ptr, where, m, sign, nw, omega.ctypes.data_as(P), eta,
+                                    spec.ctypes.data_as(P), resp.ctypes.data_as(P),
+                                    coef.ctypes.data_as(P) if coef is not None else None, ctypes.byref(steps))
+    return rc, spec, resp[0::2] + 1j * resp[1::2], coef, steps.value
 
 
 def bse_apply(h, op, k, X_ptr, Y_ptr):
@@ -233,13 +260,15 @@ class Solver:
             self.h = bse_create(self.N, aptr, bptr, self.form, self.dtype, where, self.stream.cuda_stream)
         self.nev = 0
 
-    def solve(self, nev, tol=None, ncv=0, maxit=0, seed=0, vectors=True, lock_tol=0.0, check=True):
+    def solve(self, nev, tol=None, ncv=0, maxit=0, seed=0, vectors=True, lock_tol=0.0, check=True,
+              graphs=True):
         torch = _torch()
         if tol is None:
             tol = 1e-12 if self.dtype == BSE_C128 else 1e-6
         rows = 2 * self.N if self.form == BSE_PH else self.N
         ev = torch.empty((nev, rows), dtype=self.cdtype, device=self.device) if vectors else None
-        opts = bse_solve_opts(ncv=ncv, maxit=maxit, seed=seed, v0=None, lock_tol=lock_tol)
+        opts = bse_solve_opts(ncv=ncv, maxit=maxit, seed=seed, v0=None, lock_tol=lock_tol,
+                              stream_launches=0 if graphs else 1)
         rc, vals, nconv = bse_solve_ex(self.h, nev, tol, BSE_LOWEST, opts,
                                        ev.data_ptr() if ev is not None else None)
         if check:
@@ -260,15 +289,25 @@ class Solver:
         out = Y.T
         return out.reshape(X.shape) if X.dim() == 1 else out
 
-    def backward(self, g):
+    def backward(self, g, impl=BSE_IMPL_AUTO):
         torch = _torch()
         g = np.ascontiguousarray(np.asarray(g, dtype=np.float64))
         dA = torch.empty((self.N, self.N), dtype=self.cdtype, device=self.device)
         dB = torch.empty_like(dA) if self.form == BSE_PH else None
-        rc = bse_backward(self.h, g.ctypes.data, BSE_HOST, dA.data_ptr(),
-                          dB.data_ptr() if dB is not None else None)
+        rc = bse_backward_ex(self.h, g.ctypes.data, BSE_HOST, dA.data_ptr(),
+                             dB.data_ptr() if dB is not None else None, impl)
         _check(rc, "bse_backward")
         return dA, dB
+
+    def haydock(self, d, m, omega, eta, sign=-1):
+        """Lanczos-Haydock absorption spectrum (bse_haydock): returns
+        (spectrum, response F, {"alpha", "beta", "norm2"}, steps)."""
+        torch = _torch()
+        dt = torch.as_tensor(d).to(device=self.device, dtype=torch.complex128).contiguous()
+        rc, spec, resp, coef, steps = bse_haydock(self.h, dt.data_ptr(), BSE_DEVICE, int(m), int(sign), omega, eta)
+        _check(rc, "bse_haydock")
+        coefs = {"alpha": coef[:m][:steps], "beta": coef[m:2 * m][:max(steps - 1, 0)], "norm2": coef[2 * m]}
+        return spec, resp, coefs, steps
 
     def stats(self):
         return bse_get_stats(self.h)
@@ -302,11 +341,12 @@ class BatchedSolver:
                                     BSE_PH, self.dtype, BSE_DEVICE, self.stream.cuda_stream)
         self.As = self.Bs = None      # the library holds its own packed copies
 
-    def solve(self, nev, tol=1e-6, ncv=0, maxit=0, vectors=False, check=True):
+    def solve(self, nev, tol=1e-6, ncv=0, maxit=0, vectors=False, check=True, graphs=True):
         torch = _torch()
         vecs = [torch.empty((nev, 2 * n), dtype=self.cdtype, device=self.device) for n in self.Ns] \
             if vectors else None
-        opts = bse_solve_opts(ncv=ncv, maxit=maxit, seed=0, v0=None, lock_tol=0.0)
+        opts = bse_solve_opts(ncv=ncv, maxit=maxit, seed=0, v0=None, lock_tol=0.0,
+                              stream_launches=0 if graphs else 1)
         rc, vals, nconv = bse_solve_batched(self.h, len(self.Ns), nev, tol, BSE_LOWEST, opts,
                                             [v.data_ptr() for v in vecs] if vecs else None)
         if check:

@@ -8,6 +8,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -40,6 +42,37 @@ struct ProbHost {
   std::vector<double> eval, res;
 };
 
+// A CUDA graph of 2^b consecutive Krylov steps.  The step kernels read the
+// per-problem state on the device and do nothing once a problem's subspace
+// is full, so one captured sequence serves every cycle of a solve.
+struct StepGraph {
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;            // kernels per replay
+  std::vector<cudaEvent_t> ev;       // product start/stop pairs recorded by the graph
+  bool pending = false;              // replayed since the events were last read
+};
+
+constexpr int kMaxGraphLog = 10;     // 2^10 = MAXM steps
+
+// Launch-shape tuner of the structured product.  While a handle is untuned,
+// its successive products (the solver's own, no extra work) cycle through
+// the candidate shapes; each product is timed by the CUDA events that also
+// feed bse_stats.  Once every candidate has kTuneSamples timings after its
+// first one, the shape with the lowest mean is kept for the handle and, keyed
+// by kernel variant, tile-job count and problem count, for later handles.
+constexpr int kTuneSamples = 3;
+
+struct TuneKey {
+  int variant, njobs, count;
+  bool operator<(const TuneKey& o) const {
+    if (variant != o.variant) return variant < o.variant;
+    if (njobs != o.njobs) return njobs < o.njobs;
+    return count < o.count;
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, ProdShape> g_tuned;
+
 }  // namespace
 
 struct bse_handle {
@@ -70,11 +103,31 @@ struct bse_handle {
   // adjoint tile list
   int2* adj_tiles = nullptr;
   int64_t adj_ntiles = 0;
+  int2* adj_tiles128 = nullptr;   // tensor-core adjoint
+  int64_t adj_ntiles128 = 0;
+  void* adj_panels = nullptr;
+  size_t adj_panel_bytes = 0;
+  int* adj_err = nullptr;
   double* gdev = nullptr;
   // product timing ring
   std::vector<cudaEvent_t> ev;
   int ev_used = 0;
   double ms_product = 0.0;
+  // product launch shape and its tuner state
+  ProdShape shape{0, 0};
+  bool tuned = false;
+  TuneKey tkey{};
+  std::vector<ProdShape> cands;
+  std::vector<double> tsum;
+  std::vector<int> tcnt, tseen;
+  int tnext = 0;
+  std::vector<int> ev_tag;   // candidate timed by each pair of the ring (-1: none)
+  // step graphs (valid for one subspace size) and the stream they are captured on
+  StepGraph sg[kMaxGraphLog + 1];
+  StepGraph rg;              // the restart sequence (Ritz pairs, lock decision, restart)
+  int sg_ncv = 0;
+  bool graphs = true;
+  cudaStream_t cap = nullptr;
 };
 
 namespace {
@@ -166,34 +219,86 @@ template <typename ST>
 struct Driver {
   using R = typename std::conditional<std::is_same<ST, float2>::value, float, double>::type;
   bse_handle* h;
-  explicit Driver(bse_handle* hh) : h(hh) {}
+  cudaStream_t s;                          // the handle's stream, or the capture stream
+  std::vector<cudaEvent_t>* cap_ev = nullptr;   // events of the graph being captured
+  size_t cap_n = 0;
+  explicit Driver(bse_handle* hh) : h(hh), s(hh->stream) {}
 
   void product(int mode) {
-    const bool timed = h->ev_used + 2 <= (int)h->ev.size();
-    if (timed) cudaEventRecord(h->ev[h->ev_used], h->stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ProdShape shape = h->shape;
+    int tag = -1;
+    if (!h->tuned && !cap_ev && !h->cands.empty()) {
+      tag = h->tnext++ % (int)h->cands.size();
+      shape = h->cands[tag];
+    }
+    if (cap_ev) {
+      if (cap_n + 2 <= cap_ev->size()) {
+        e0 = (*cap_ev)[cap_n];
+        e1 = (*cap_ev)[cap_n + 1];
+        cap_n += 2;
+        cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
+      }
+    } else if (h->ev_used + 2 <= (int)h->ev.size()) {
+      e0 = h->ev[h->ev_used];
+      e1 = h->ev[h->ev_used + 1];
+      h->ev_tag[h->ev_used / 2] = tag;
+      h->ev_used += 2;
+      cudaEventRecord(e0, s);
+    }
     if (h->df)
       launch_product_df(h->dprobs, h->djobs, h->njobs, h->count, h->maxnT, mode, nullptr, h->ph != 0, h->split,
-                        h->stream);
+                        shape, s);
     else
       launch_product<ST, R>(h->dprobs, h->djobs, h->njobs, h->count, h->maxnT, mode, 1, nullptr, h->ph != 0,
-                            h->stream);
-    if (timed) {
-      cudaEventRecord(h->ev[h->ev_used + 1], h->stream);
-      h->ev_used += 2;
+                            shape, s);
+    if (e1) {
+      if (cap_ev) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+      else cudaEventRecord(e1, s);
     }
+  }
+
+  static double elapsed(const std::vector<cudaEvent_t>& ev, size_t n) {
+    double sum = 0.0;
+    for (size_t i = 0; i + 1 < n; i += 2) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) sum += ms;
+    }
+    return sum;
   }
 
   void harvest_events() {
     for (int i = 0; i + 1 < h->ev_used; i += 2) {
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) == cudaSuccess) h->ms_product += ms;
+      if (cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) != cudaSuccess) continue;
+      h->ms_product += ms;
+      const int tag = h->ev_tag[i / 2];
+      if (tag >= 0 && !h->tuned && h->tseen[tag]++ > 0) {   // the first timing of a shape is a warm-up
+        h->tsum[tag] += ms;
+        h->tcnt[tag] += 1;
+      }
     }
     h->ev_used = 0;
+    if (!h->tuned && !h->cands.empty() &&
+        *std::min_element(h->tcnt.begin(), h->tcnt.end()) >= kTuneSamples) {
+      int best = 0;
+      for (int c = 1; c < (int)h->cands.size(); ++c)
+        if (h->tsum[c] / h->tcnt[c] < h->tsum[best] / h->tcnt[best]) best = c;
+      h->shape = h->cands[best];
+      h->tuned = true;
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tuned[h->tkey] = h->shape;
+    }
+    for (StepGraph& g : h->sg) {
+      if (!g.pending) continue;
+      h->ms_product += elapsed(g.ev, g.ev.size());
+      g.pending = false;
+    }
   }
 
   void cgs(int pass) {
     const int ncol = h->ncv + 1 + h->ncv;
-    launch_step_cgs<ST>(h->dprobs, h->count, h->ph, h->maxnrb, h->maxNpad, ncol, pass, h->stream);
+    launch_step_cgs<ST>(h->dprobs, h->count, h->ph, h->maxnrb, h->maxNpad, ncol, pass, s);
   }
 
   void step() {
@@ -201,7 +306,124 @@ struct Driver {
     cgs(0);
     cgs(1);
     if (h->ph) product(PM_STEP_MPLUS);
-    launch_step_normalize<ST>(h->dprobs, h->count, h->ph, h->maxnrb, h->maxNpad, 0, h->stream);
+    launch_step_normalize<ST>(h->dprobs, h->count, h->ph, h->maxnrb, h->maxNpad, 0, s);
+  }
+
+  // record 2^b steps into h->sg[b]; false (and graphs off for the handle)
+  // when capture or instantiation is refused
+  bool capture(int b) {
+    StepGraph& g = h->sg[b];
+    const int n = 1 << b;
+    const size_t nev = (size_t)(h->ph ? 4 : 2) * n;
+    while (g.ev.size() < nev) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); h->graphs = false; return false; }
+      g.ev.push_back(e);
+    }
+    if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      h->cap = nullptr;
+      h->graphs = false;
+      return false;
+    }
+    if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaGetLastError();
+      h->graphs = false;
+      return false;
+    }
+    const long long c0 = launch_counter();
+    s = h->cap;
+    cap_ev = &g.ev;
+    cap_n = 0;
+    for (int i = 0; i < n; ++i) step();
+    s = h->stream;
+    cap_ev = nullptr;
+    g.launches = launch_counter() - c0;
+    launch_counter() = c0;                  // counted again at every replay
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      g.exec = nullptr;
+      h->graphs = false;
+      return false;
+    }
+    return true;
+  }
+
+  // `steps` Krylov steps: graphs of 2^b steps for the binary digits of
+  // `steps` (each replayed at most once per cycle, so every event pair of a
+  // replay is read before it is recorded again), or plain launches
+  void run_steps(int steps) {
+    if (!h->tuned) {                       // shapes still being compared: one launch at a time
+      for (; steps > 0; --steps) step();
+      return;
+    }
+    if (h->graphs && h->sg_ncv != h->ncv) {
+      drop_graphs();
+      h->sg_ncv = h->ncv;
+    }
+    for (int b = kMaxGraphLog; b >= 0 && steps > 0; --b) {
+      const int n = 1 << b;
+      if (steps < n) continue;
+      StepGraph& g = h->sg[b];
+      if (h->graphs && (g.exec || capture(b)) && cudaGraphLaunch(g.exec, h->stream) == cudaSuccess) {
+        launch_counter() += g.launches;
+        g.pending = true;
+      } else {
+        cudaGetLastError();
+        for (int i = 0; i < n; ++i) step();
+      }
+      steps -= n;
+    }
+    for (; steps > 0; --steps) step();     // only when steps >= 2^(kMaxGraphLog+1)
+  }
+
+  void restart_seq(cudaStream_t st) {
+    launch_ritz(h->dprobs, h->count, h->ncv, st);
+    launch_lock_decide_form(h->dprobs, h->count, h->ph, st);
+    launch_restart<ST>(h->dprobs, h->count, h->ph, h->maxNpad, h->ncv, st);
+  }
+
+  // the restart sequence reads every decision from KState, so it replays as
+  // one graph too (captured with the step graphs, for one subspace size)
+  void run_restart() {
+    if (h->graphs && h->sg_ncv != h->ncv) {
+      drop_graphs();
+      h->sg_ncv = h->ncv;
+    }
+    StepGraph& g = h->rg;
+    if (h->graphs && !g.exec && (h->cap || cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) == cudaSuccess) &&
+        cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+      const long long c0 = launch_counter();
+      restart_seq(h->cap);
+      g.launches = launch_counter() - c0;
+      launch_counter() = c0;
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) g.exec = nullptr;
+    }
+    cudaGetLastError();
+    if (h->graphs && g.exec && cudaGraphLaunch(g.exec, h->stream) == cudaSuccess) {
+      launch_counter() += g.launches;
+      return;
+    }
+    cudaGetLastError();
+    restart_seq(h->stream);
+  }
+
+  void drop_graphs() {
+    for (StepGraph& g : h->sg) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+      g.pending = false;
+    }
+    if (h->rg.exec) cudaGraphExecDestroy(h->rg.exec);
+    h->rg.exec = nullptr;
   }
 
   void fresh_chain(uint64_t seed, const void* v0) {
@@ -249,12 +471,10 @@ struct Driver {
         continue;
       }
       if (steps > 0) {
-        for (int s = 0; s < steps; ++s) step();
+        run_steps(steps);
         continue;
       }
-      launch_ritz(h->dprobs, h->count, h->ncv, h->stream);
-      launch_lock_decide_form(h->dprobs, h->count, h->ph, h->stream);
-      launch_restart<ST>(h->dprobs, h->count, h->ph, h->maxNpad, h->ncv, h->stream);
+      run_restart();
     }
     return BSE_OK;
   }
@@ -419,6 +639,7 @@ int solve_impl(bse_handle* h, int nev, double tol, const bse_solve_opts* opts, d
   const uint64_t seed = opts && opts->seed ? opts->seed : 12345ull;
   const double lock_tol = opts && opts->lock_tol > 0.0 ? opts->lock_tol : tol * 0.25;
   const void* v0 = (opts && h->count == 1) ? opts->v0 : nullptr;
+  const bool graphs = !(opts && opts->stream_launches);
   int rc = alloc_solve(h, ncv);
   if (rc) return rc;
   h->ncv = ncv;
@@ -440,6 +661,7 @@ int solve_impl(bse_handle* h, int nev, double tol, const bse_solve_opts* opts, d
   if (h->ev.empty()) {
     h->ev.resize(4 * MAXM + 8);
     for (auto& e : h->ev) cudaEventCreate(&e);
+    h->ev_tag.assign(h->ev.size() / 2, -1);
   }
   h->ev_used = 0;
   h->ms_product = 0.0;
@@ -449,6 +671,7 @@ int solve_impl(bse_handle* h, int nev, double tol, const bse_solve_opts* opts, d
   cudaEventRecord(e0, h->stream);
   const long long launches0 = launch_counter();
   Driver<ST> drv(h);
+  h->graphs = graphs;
   rc = drv.iterate(seed, v0);
   if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
   int worst = BSE_OK;
@@ -491,8 +714,36 @@ int solve_impl(bse_handle* h, int nev, double tol, const bse_solve_opts* opts, d
   h->stats.ms_total = ms;
   h->stats.ms_product = h->ms_product;
   h->stats.launches = launch_counter() - launches0;
+  h->stats.shape_ctas_per_sm = h->shape.ctas_per_sm;
+  h->stats.shape_strided = h->shape.strided;
+  h->stats.tuned = h->tuned ? 1 : 0;
   h->solved = true;
   return worst;
+}
+
+// candidate launch shapes of the handle's product kernel (see TuneKey)
+void setup_tuner(bse_handle* h) {
+  const int occ = h->df ? product_df_occupancy(h->ph != 0, h->split)
+                        : (h->vs == sizeof(float2) ? product_occupancy<float2, float>(h->ph != 0)
+                                                   : product_occupancy<double2, double>(h->ph != 0));
+  const bool batch = h->count > 1;
+  h->cands.clear();
+  for (int c = 1; c <= occ; ++c) {
+    if (!batch) h->cands.push_back(ProdShape{c, 0});
+    h->cands.push_back(ProdShape{c, 1});
+  }
+  h->cands.push_back(ProdShape{-1, 0});
+  const size_t n = h->cands.size();
+  h->tsum.assign(n, 0.0);
+  h->tcnt.assign(n, 0);
+  h->tseen.assign(n, 0);
+  h->tnext = 0;
+  h->shape = ProdShape{0, batch ? 1 : 0};
+  h->tkey = TuneKey{h->dtype * 2 + h->ph, h->njobs, h->count};
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find(h->tkey);
+  h->tuned = it != g_tuned.end();
+  if (h->tuned) h->shape = it->second;
 }
 
 // ------------------------------------------------------------------ apply helpers
@@ -558,7 +809,9 @@ int apply_impl(bse_handle* h, int op, int k, const void* X, void* Y) {
   const bool hasB = h->ph != 0;
   if ((op != BSE_OP_A) && !hasB) return BSE_EINVAL;
   int rc;
-  if (op != BSE_OP_H && k == 1) {
+  // A alone on complex128 PH tiles (P, Q) goes through the row-block kernel, which unpacks A
+  const bool pq_a = hasB && op == BSE_OP_A && !h->tiles64;
+  if (op != BSE_OP_H && k == 1 && !pq_a) {
     // the streaming tile kernel (the solver's hot path), padded copies in/out
     if (!q.w || q.ncv == 0) {
       if ((rc = alloc_solve(h, std::min<int64_t>(q.N, 8) > 1 ? (int)std::min<int64_t>(q.N, 8) : 1))) return rc;
@@ -573,10 +826,10 @@ int apply_impl(bse_handle* h, int op, int k, const void* X, void* Y) {
     io.sB = op == BSE_OP_A ? 0.0 : (op == BSE_OP_MPLUS ? 1.0 : -1.0);
     if (h->df && h->split)   // complex128 handle: the solver's double-FP32 product
       launch_product_df(h->dprobs, h->djobs, h->njobs, 1, h->maxnT, PM_GENERIC, &io, hasB && op != BSE_OP_A,
-                        true, h->stream);
+                        true, h->shape, h->stream);
     else
       launch_product<ST, R>(h->dprobs, h->djobs, h->njobs, 1, h->maxnT, PM_GENERIC, 1, &io,
-                            hasB && op != BSE_OP_A, h->stream);
+                            hasB && op != BSE_OP_A, h->shape, h->stream);
     CK(cudaMemcpyAsync(Y, q.pw, h->es * (size_t)N, cudaMemcpyDeviceToDevice, h->stream));
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
@@ -611,8 +864,9 @@ int apply_impl(bse_handle* h, int op, int k, const void* X, void* Y) {
     sB = op == BSE_OP_A ? 0.0 : (op == BSE_OP_MPLUS ? 1.0 : -1.0);
     xb = nullptr;  // conj(XA)
   }
+  // P, Q tiles always go through the unpacking variant (sB = 0 drops the B half)
   launch_rowblock<ST, R>(h->dprobs, 0, q.nT, XA, xb, (int)Npad, sB, U, (int)Npad, kc,
-                         hasB && op != BSE_OP_A, h->stream);
+                         hasB && (op != BSE_OP_A || !h->tiles64), h->stream);
   count_launch();
   k_hz_out<ST, CT><<<dim3((unsigned)((N + 255) / 256), k), 256, 0, h->stream>>>(U, N, Npad, k, op, (ST*)Y);
   CK(cudaGetLastError());
@@ -621,7 +875,7 @@ int apply_impl(bse_handle* h, int op, int k, const void* X, void* Y) {
 }
 
 template <typename ST>
-int backward_impl(bse_handle* h, const double* g, int where, void* dA, void* dB) {
+int backward_impl(bse_handle* h, const double* g, int where, void* dA, void* dB, int impl) {
   using R = typename std::conditional<std::is_same<ST, float2>::value, float, double>::type;
   ProbHost& q = h->p[0];
   const int k = q.nconv;
@@ -650,10 +904,194 @@ int backward_impl(bse_handle* h, const double* g, int where, void* dA, void* dB)
     CK(cudaMemcpyAsync(h->adj_tiles, t.data(), sizeof(int2) * t.size(), cudaMemcpyHostToDevice, h->stream));
   }
   const int64_t ldz = h->ph ? 2 * q.Npad : q.Npad;
-  launch_adjoint2<ST, R>(q.Z, ldz, q.Npad, q.N, k, h->gdev, h->ph, h->adj_tiles, h->adj_ntiles, (ST*)dA,
-                         (ST*)dB, h->stream);
+  const bool tensor = std::is_same<ST, float2>::value && impl != BSE_IMPL_CUDA_CORES;
+  if (!tensor) {
+    launch_adjoint2<ST, R>(q.Z, ldz, q.Npad, q.N, k, h->gdev, h->ph, h->adj_tiles, h->adj_ntiles, (ST*)dA,
+                           (ST*)dB, h->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    return BSE_OK;
+  }
+  // complex64 outputs: rank-2k update on the tensor cores (3xTF32)
+  if (!h->adj_tiles128) {
+    const int nb = (int)((q.N + 127) / 128);
+    std::vector<int2> t;
+    t.reserve((size_t)nb * (nb + 1) / 2);
+    for (int I = 0; I < nb; ++I)
+      for (int J = I; J < nb; ++J) t.push_back(make_int2(I, J));
+    h->adj_ntiles128 = (int64_t)t.size();
+    if ((rc = dalloc((void**)&h->adj_tiles128, sizeof(int2) * t.size()))) return rc;
+    CK(cudaMemcpyAsync(h->adj_tiles128, t.data(), sizeof(int2) * t.size(), cudaMemcpyHostToDevice, h->stream));
+  }
+  const size_t pb = adjoint_tc_panel_bytes(q.N, k, h->ph);
+  if (pb > h->adj_panel_bytes) {
+    dfree(h->adj_panels);
+    h->adj_panel_bytes = 0;
+    if ((rc = dalloc(&h->adj_panels, pb))) return rc;
+    h->adj_panel_bytes = pb;
+  }
+  if (!h->adj_err && (rc = dalloc((void**)&h->adj_err, sizeof(int)))) return rc;
+  const int r = launch_adjoint_tc(q.Z, ldz, q.Npad, q.N, k, h->gdev, h->ph, h->adj_tiles128, h->adj_ntiles128,
+                                  (float*)h->adj_panels, h->adj_err, (float2*)dA, (float2*)dB, h->stream);
+  if (r < 0) return BSE_ECUDA;
+  if (r > 0) return BSE_ETIMEOUT;
+  return BSE_OK;
+}
+
+// ------------------------------------------------------------------ Haydock spectrum
+template <typename ST>
+int haydock_impl(bse_handle* h, const void* d, int where, int m, int sign, int nw, const double* omega, double eta,
+                 double* spectrum_out, double* response_out, double* coef_out, int* steps_out) {
+  using R = typename std::conditional<std::is_same<ST, float2>::value, float, double>::type;
+  ProbHost& q0 = h->p[0];
+  int rc;
+  if (!q0.w || q0.ncv == 0) {      // the product's partial-sum scratch lives with the solve buffers
+    if ((rc = alloc_solve(h, std::min<int64_t>(q0.N, 8) > 1 ? (int)std::min<int64_t>(q0.N, 8) : 1))) return rc;
+    if ((rc = upload_probs(h))) return rc;
+  }
+  const int64_t N = q0.N, Npad = q0.Npad;
+  const bool ph = h->ph != 0;
+  const int np = haydock_partials();
+  // one allocation: 6 vectors, partial sums, alpha, beta, state, frequencies, output, staged d
+  const size_t vb = sizeof(ST) * (size_t)Npad;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+  const size_t o_vec = take(6 * vb), o_part = take(sizeof(double) * np), o_al = take(sizeof(double) * m),
+               o_be = take(sizeof(double) * m), o_st = take(sizeof(HdState)), o_om = take(sizeof(double) * nw),
+               o_out = take(sizeof(double) * 2 * nw), o_d = take(where == BSE_HOST ? sizeof(double2) * N : 0);
+  char* buf = nullptr;
+  if ((rc = dalloc((void**)&buf, off))) return rc;
+  struct Free { char* b; ~Free() { cudaFree(b); } } guard{buf};
+  ST* r = (ST*)(buf + o_vec);
+  ST* pr = r + Npad;
+  ST* w = pr + Npad;
+  ST* q = w + Npad;
+  ST* qprev = q + Npad;
+  ST* p = qprev + Npad;
+  double* part = (double*)(buf + o_part);
+  double* alpha = (double*)(buf + o_al);
+  double* beta = (double*)(buf + o_be);
+  HdState* st = (HdState*)(buf + o_st);
+  double* om = (double*)(buf + o_om);
+  double* out = (double*)(buf + o_out);
+  const double2* dd = (const double2*)d;
+  cudaStream_t s0 = h->stream;
+  if (where == BSE_HOST) {
+    CK(cudaMemcpyAsync(buf + o_d, d, sizeof(double2) * N, cudaMemcpyHostToDevice, s0));
+    dd = (const double2*)(buf + o_d);
+  }
+  HdState hs{0, m, 0, 0, 0.0};
+  CK(cudaMemcpyAsync(st, &hs, sizeof(HdState), cudaMemcpyHostToDevice, s0));
+  CK(cudaMemcpyAsync(om, omega, sizeof(double) * nw, cudaMemcpyHostToDevice, s0));
+  const double sK = ph ? (double)sign : 0.0, sK2 = -sK;   // K = M- (s = -1) or M+ (s = +1); K' the other
+  auto product = [&](const ST* x, ST* y, double sB, cudaStream_t s) {
+    GenericIO io{};
+    io.xa = x;
+    io.y = y;
+    io.sB = sB;
+    if (h->df)
+      launch_product_df(h->dprobs, h->djobs, h->njobs, 1, h->maxnT, PM_GENERIC, &io, ph, h->split, h->shape, s);
+    else
+      launch_product<ST, R>(h->dprobs, h->djobs, h->njobs, 1, h->maxnT, PM_GENERIC, 1, &io, ph, h->shape, s);
+  };
+  auto step = [&](cudaStream_t s) {
+    if (ph) product(p, w, sK2, s);
+    else product(q, w, 0.0, s);
+    launch_hd_dot<ST>(ph ? p : q, w, Npad, part, s);
+    launch_hd_scalar(st, part, alpha, beta, 1, s);
+    launch_hd_axpy<ST>(st, alpha, beta, w, q, qprev, r, Npad, s);
+    if (ph) {
+      product(r, pr, sK, s);
+      launch_hd_dot<ST>(r, pr, Npad, part, s);
+    } else {
+      launch_hd_dot<ST>(r, r, Npad, part, s);
+    }
+    launch_hd_scalar(st, part, alpha, beta, 2, s);
+    launch_hd_scale<ST>(st, beta, r, ph ? pr : nullptr, q, qprev, ph ? p : nullptr, Npad, 0, s);
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s0);
+  const long long launches0 = launch_counter();
+  // start: q_0 = d / sqrt(<d, d>_K), p_0 = K q_0
+  launch_hd_load<ST>(dd, N, Npad, r, s0);
+  if (ph) {
+    product(r, pr, sK, s0);
+    launch_hd_dot<ST>(r, pr, Npad, part, s0);
+  } else {
+    launch_hd_dot<ST>(r, r, Npad, part, s0);
+  }
+  launch_hd_scalar(st, part, alpha, beta, 0, s0);
+  launch_hd_scale<ST>(st, beta, r, ph ? pr : nullptr, q, qprev, ph ? p : nullptr, Npad, 1, s0);
+  // the steps: one captured step replayed m times (stream launches if capture is refused)
+  cudaGraphExec_t exec = nullptr;
+  long long per_step = 0;
+  if (h->cap || cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) == cudaSuccess) {
+    if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+      const long long c0 = launch_counter();
+      step(h->cap);
+      per_step = launch_counter() - c0;
+      launch_counter() = c0;
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamEndCapture(h->cap, &graph) == cudaSuccess && graph) {
+        if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+        cudaGraphDestroy(graph);
+      }
+    }
+  }
+  cudaGetLastError();
+  for (int j = 0; j < m; ++j) {
+    if (exec && cudaGraphLaunch(exec, s0) == cudaSuccess) {
+      launch_counter() += per_step;
+    } else {
+      cudaGetLastError();
+      step(s0);
+    }
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  launch_hd_cf(st, alpha, beta, nw, om, eta, ph ? 1 : 0, out, s0);
+  cudaEventRecord(e1, s0);
+  std::vector<double> hout(2 * (size_t)nw);
+  CK(cudaMemcpyAsync(hout.data(), out, sizeof(double) * 2 * nw, cudaMemcpyDeviceToHost, s0));
+  CK(cudaMemcpyAsync(&hs, st, sizeof(HdState), cudaMemcpyDeviceToHost, s0));
+  std::vector<double> hal, hbe;
+  if (coef_out) {
+    hal.resize(m);
+    hbe.resize(m);
+    CK(cudaMemcpyAsync(hal.data(), alpha, sizeof(double) * m, cudaMemcpyDeviceToHost, s0));
+    CK(cudaMemcpyAsync(hbe.data(), beta, sizeof(double) * m, cudaMemcpyDeviceToHost, s0));
+  }
+  CK(cudaStreamSynchronize(s0));
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(h->stream));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int i = 0; i < nw; ++i) {
+    spectrum_out[i] = -hout[2 * (size_t)i + 1] / M_PI;
+    if (response_out) {
+      response_out[2 * (size_t)i] = hout[2 * (size_t)i];
+      response_out[2 * (size_t)i + 1] = hout[2 * (size_t)i + 1];
+    }
+  }
+  if (coef_out) {
+    for (int j = 0; j < m; ++j) {
+      coef_out[j] = j < hs.nsteps ? hal[j] : 0.0;
+      coef_out[m + j] = j + 1 < hs.nsteps ? hbe[j] : 0.0;
+    }
+    coef_out[2 * (size_t)m] = hs.n2;
+  }
+  if (steps_out) *steps_out = hs.nsteps;
+  h->stats = bse_stats{};
+  h->stats.steps = hs.nsteps;
+  h->stats.passes = ph ? 2 * (int64_t)m + 1 : (int64_t)m;
+  h->stats.ms_total = ms;
+  h->stats.launches = launch_counter() - launches0;
+  h->stats.shape_ctas_per_sm = h->shape.ctas_per_sm;
+  h->stats.shape_strided = h->shape.strided;
+  h->stats.tuned = h->tuned ? 1 : 0;
+  if (!(hs.n2 > 0.0)) return BSE_ENOTPD;
   return BSE_OK;
 }
 
@@ -724,6 +1162,8 @@ int bse_create_batched(int count, const int64_t* N, const void* const* A, const 
     } else {
       rc = pack_matrix<double2>(h, (const double2*)A[i], q.N, q.nT, 1, where, (double2*)q.A);
       if (!rc && h->ph) rc = pack_matrix<double2>(h, (const double2*)B[i], q.N, q.nT, 0, where, (double2*)q.B);
+      // complex128 PH tiles are kept as P = A + B, Q = A - B (8 FMAs per element pair)
+      if (!rc && h->ph) launch_pq_combine((double2*)q.A, (double2*)q.B, q.ntiles * TS * TS, h->stream);
       if (!rc && h->df) {
         const int64_t nel = q.ntiles * TS * TS;
         if (!(rc = dalloc(&q.Ahl, sizeof(float4) * (size_t)nel)))
@@ -753,6 +1193,7 @@ int bse_create_batched(int count, const int64_t* N, const void* const* A, const 
   if (rc == BSE_OK) rc = dalloc((void**)&h->dprobs, sizeof(Prob) * count);
   if (rc == BSE_OK) rc = dalloc((void**)&h->dstate, sizeof(KState) * count);
   if (rc == BSE_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = BSE_ECUDA;
+  if (rc == BSE_OK) setup_tuner(h);
   if (rc != BSE_OK) {
     bse_destroy(h);
     return rc;
@@ -788,15 +1229,21 @@ int bse_solve_batched(bse_handle* h, int nev, double tol, int which, const bse_s
   return solve_impl<double2>(h, nev, tol, opts, eval_out, evec_out, nconv_out);
 }
 
-int bse_backward(bse_handle* h, const double* dL_dlambda, int where, void* dA, void* dB) {
+int bse_backward_ex(bse_handle* h, const double* dL_dlambda, int where, void* dA, void* dB, int impl) {
   if (!h || !dL_dlambda || !dA) return BSE_EINVAL;
+  if (impl < BSE_IMPL_AUTO || impl > BSE_IMPL_TENSOR_CORES) return BSE_EINVAL;
+  if (impl == BSE_IMPL_TENSOR_CORES && !is_c64(h->dtype)) return BSE_EINVAL;
   if (where != BSE_HOST && where != BSE_DEVICE) return BSE_EINVAL;
   if (h->count != 1) return BSE_EINVAL;
   if (h->ph && !dB) return BSE_EINVAL;
   if (!h->ph && dB) return BSE_EINVAL;
   if (!h->solved) return BSE_ESTATE;
-  if (is_c64(h->dtype)) return backward_impl<float2>(h, dL_dlambda, where, dA, dB);
-  return backward_impl<double2>(h, dL_dlambda, where, dA, dB);
+  if (is_c64(h->dtype)) return backward_impl<float2>(h, dL_dlambda, where, dA, dB, impl);
+  return backward_impl<double2>(h, dL_dlambda, where, dA, dB, impl);
+}
+
+int bse_backward(bse_handle* h, const double* dL_dlambda, int where, void* dA, void* dB) {
+  return bse_backward_ex(h, dL_dlambda, where, dA, dB, BSE_IMPL_AUTO);
 }
 
 int bse_apply(bse_handle* h, int op, int k, const void* X, void* Y) {
@@ -804,6 +1251,19 @@ int bse_apply(bse_handle* h, int op, int k, const void* X, void* Y) {
   if (op < BSE_OP_A || op > BSE_OP_H) return BSE_EINVAL;
   if (is_c64(h->dtype)) return apply_impl<float2>(h, op, k, X, Y);
   return apply_impl<double2>(h, op, k, X, Y);
+}
+
+int bse_haydock(bse_handle* h, const void* d, int where, int m, int sign, int nw, const double* omega, double eta,
+                double* spectrum_out, double* response_out, double* coef_out, int* steps_out) {
+  if (!h || !d || !omega || !spectrum_out || h->count != 1) return BSE_EINVAL;
+  if (where != BSE_HOST && where != BSE_DEVICE) return BSE_EINVAL;
+  if (m < 1 || m > 1000000 || nw < 1 || !(eta > 0.0) || !std::isfinite(eta)) return BSE_EINVAL;
+  if (h->ph && sign != 1 && sign != -1) return BSE_EINVAL;
+  if (h->vs == sizeof(float2))
+    return haydock_impl<float2>(h, d, where, m, sign, nw, omega, eta, spectrum_out, response_out, coef_out,
+                                steps_out);
+  return haydock_impl<double2>(h, d, where, m, sign, nw, omega, eta, spectrum_out, response_out, coef_out,
+                               steps_out);
 }
 
 int bse_get_stats(const bse_handle* h, bse_stats* out) {
@@ -828,8 +1288,17 @@ int bse_destroy(bse_handle* h) {
   dfreet(h->djobs);
   dfree(h->post);
   dfreet(h->adj_tiles);
+  dfreet(h->adj_tiles128);
+  dfree(h->adj_panels);
+  dfreet(h->adj_err);
   dfreet(h->gdev);
   for (auto& e : h->ev) cudaEventDestroy(e);
+  for (StepGraph& g : h->sg) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto& e : g.ev) cudaEventDestroy(e);
+  }
+  if (h->rg.exec) cudaGraphExecDestroy(h->rg.exec);
+  if (h->cap) cudaStreamDestroy(h->cap);
   delete h;
   return BSE_OK;
 }

@@ -152,19 +152,69 @@ inline void count_launch(int n = 1) { launch_counter() += n; }
 template <typename TIn, typename TSt>
 void launch_pack_row(const TIn* rows, int64_t N, int nT, int I, int herm, TSt* dst, cudaStream_t s);
 
+// Launch shape of the streaming product, chosen per handle by measurement
+// (bse_api.cu): CTAs per SM (0 = as many as fit, -1 = one CTA per tile) and
+// the walk of a CTA over the job list (0 = one contiguous run, 1 = every
+// gridDim.x-th job, which keeps the load even when some problems of a batch
+// have finished and their jobs are skipped).
+struct ProdShape {
+  int ctas_per_sm;
+  int strided;
+};
+
+// complex128 PH storage: tiles of A and B become P = A + B and Q = A - B (k_product.cu)
+void launch_pq_combine(double2* a, double2* b, int64_t n, cudaStream_t s);
+
 // products (k_product.cu); ST = storage complex type, R = compute real type
 template <typename ST, typename R>
 void launch_product(const Prob* dprobs, const TileJob* jobs, int njobs, int nprob, int maxnT,
-                    int mode, int K, const GenericIO* io_host, bool hasB, cudaStream_t s);
+                    int mode, int K, const GenericIO* io_host, bool hasB, ProdShape shape, cudaStream_t s);
+// resident CTAs per SM of the tile kernel launch_product / launch_product_df would use
+template <typename ST, typename R>
+int product_occupancy(bool hasB);
+int product_df_occupancy(bool hasB, bool split);
+// grid of the tile kernels for a shape, given their occupancy
+int product_grid(int occ, ProdShape shape, int njobs);
 template <typename ST, typename R>
 void launch_rowblock(const Prob* dprobs, int prob, int nT, const void* xa, const void* xb, int ldx,
                      double sB, void* y, int ldy, int K, bool hasB, cudaStream_t s);
 // complex128 products in double-FP32 arithmetic on the split tiles (k_product.cu)
 // split = true: float4 split complex128 tiles; false: complex64 tiles (exact in FP32)
 void launch_product_df(const Prob* dprobs, const TileJob* jobs, int njobs, int nprob, int maxnT,
-                       int mode, const GenericIO* io_host, bool hasB, bool split, cudaStream_t s);
+                       int mode, const GenericIO* io_host, bool hasB, bool split, ProdShape shape,
+                       cudaStream_t s);
 void launch_split_tiles(const double2* packed, int64_t nelem, float4* split, cudaStream_t s);
 void launch_prod_reduce_d(const Prob* dprobs, int nprob, int maxnT, int mode, GenericIO io, cudaStream_t s);
+
+// Lanczos-Haydock spectrum (k_haydock.cu); device-resident recurrence state
+struct HdState {
+  int j;        // current step
+  int m;        // step limit
+  int done;     // the Krylov space became invariant (or <d, d>_K was not positive)
+  int nsteps;   // valid coefficients: alpha[0, nsteps), beta[0, nsteps - 1)
+  double n2;    // <d, d>_K (TDA: |d|^2)
+};
+int haydock_partials();   // length of the partial-sum array of launch_hd_dot
+template <typename ST>
+void launch_hd_dot(const ST* x, const ST* y, int64_t n, double* partial, cudaStream_t s);
+void launch_hd_scalar(HdState* st, const double* partial, double* alpha, double* beta, int which, cudaStream_t s);
+template <typename ST>
+void launch_hd_axpy(const HdState* st, const double* alpha, const double* beta, const ST* w, const ST* q,
+                    const ST* qprev, ST* r, int64_t n, cudaStream_t s);
+template <typename ST>
+void launch_hd_scale(const HdState* st, const double* beta, const ST* r, const ST* pr, ST* q, ST* qprev, ST* p,
+                     int64_t n, int init, cudaStream_t s);
+template <typename ST>
+void launch_hd_load(const double2* d, int64_t N, int64_t Npad, ST* x, cudaStream_t s);
+void launch_hd_cf(const HdState* st, const double* alpha, const double* beta, int nw, const double* omega,
+                  double eta, int ph, double* out, cudaStream_t s);
+
+// tensor-core adjoint for complex64 outputs (k_adjoint_tc.cu); tiles128 lists
+// the 128 x 128 output tiles (I <= J).  Returns 0, 1 (device wait expired), -1 (CUDA error).
+size_t adjoint_tc_panel_bytes(int64_t N, int k, int ph);
+int launch_adjoint_tc(const double2* Z, int64_t ldz, int64_t Npad, int64_t N, int k, const double* g, int ph,
+                      const int2* tiles128, int64_t ntiles, float* panels, int* derr, float2* dA, float2* dB,
+                      cudaStream_t s);
 
 // Krylov kernels (k_krylov.cu)
 template <typename ST>

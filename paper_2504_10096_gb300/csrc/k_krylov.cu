@@ -46,11 +46,14 @@ __device__ __forceinline__ double2 dshfl(double2 v, int m) {
 
 // ---------------------------------------------------------------- CGS2 dots
 // cpart[rb][c] = sum_{rows in block rb} conj(Q[row, col(c)]) w[row],
-// Q = P (PH) or V (TDA).  grid (ceil(maxcols/8), maxnrb, nprob), 8 warps.
+// Q = P (PH) or V (TDA).  grid (ceil(maxcols/2), maxnrb, nprob), 8 warps: two
+// columns per CTA, four warps per column, each warp a quarter of the block
+// rows; the four partial sums meet in shared memory (fixed order).
 template <typename ST>
 __global__ void __launch_bounds__(256)
 k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec) {
   using R = typename RealOf<ST>::T;
+  __shared__ double2 red[2][4];
   const Prob& p = probs[blockIdx.z];
   const KState* st = p.st;
   if (!kphase(st, newvec)) return;
@@ -59,31 +62,45 @@ k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec) {
   const int j = st->j;
   const int nset = (j + 1) + (ph ? st->ntw : 0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = blockIdx.x * 8 + warp;
-  if (c >= nset) return;
-  const int col = set_col(c, j, p.ncv);
-  const ST* Q = (const ST*)(ph ? p.P : p.V) + (int64_t)col * p.Npad;
-  const ST* w = (const ST*)p.w;
-  const int64_t r0 = (int64_t)rb * ROWBLK;
-  const int64_t r1 = min((int64_t)p.Npad, r0 + ROWBLK);
-  ST acc = czero<ST>();
-  if (ph) {   // K-inner products are real: Re(conj(q) w) only
-    R a1 = 0, a2 = 0;   // two chains (x and y products) for more ILP
+  const int half = warp >> 2, quarter = warp & 3;
+  const int c = blockIdx.x * 2 + half;
+  if (blockIdx.x * 2 >= nset) return;                     // whole CTA
+  double2 a = mk(0.0, 0.0);
+  if (c < nset) {
+    const int col = set_col(c, j, p.ncv);
+    const ST* Q = (const ST*)(ph ? p.P : p.V) + (int64_t)col * p.Npad;
+    const ST* w = (const ST*)p.w;
+    const int64_t r0 = (int64_t)rb * ROWBLK + quarter * (ROWBLK / 4);
+    const int64_t r1 = min((int64_t)p.Npad, r0 + ROWBLK / 4);
+    if (ph) {   // K-inner products are real: Re(conj(q) w) only
+      R a1 = 0, a2 = 0;   // two chains (x and y products) for more ILP
 #pragma unroll 8
-    for (int64_t r = r0 + lane; r < r1; r += 32) {
-      const ST q = __ldg(Q + r), x = __ldg(w + r);
-      a1 = fma(q.x, x.x, a1);
-      a2 = fma(q.y, x.y, a2);
+      for (int64_t r = r0 + lane; r < r1; r += 32) {
+        const ST q = __ldg(Q + r), x = __ldg(w + r);
+        a1 = fma(q.x, x.x, a1);
+        a2 = fma(q.y, x.y, a2);
+      }
+      a = mk((double)a1 + (double)a2, 0.0);
+    } else {
+      ST acc = czero<ST>();
+#pragma unroll 8
+      for (int64_t r = r0 + lane; r < r1; r += 32) cfmac(acc, __ldg(Q + r), __ldg(w + r));
+      a = mk((double)acc.x, (double)acc.y);
     }
-    acc.x = a1 + a2;
-  } else {
-#pragma unroll 8
-    for (int64_t r = r0 + lane; r < r1; r += 32) cfmac(acc, __ldg(Q + r), __ldg(w + r));
-  }
-  double2 a = mk((double)acc.x, (double)acc.y);
 #pragma unroll
-  for (int m = 16; m >= 1; m >>= 1) a = cadd(a, dshfl(a, m));
-  if (lane == 0) ((double2*)p.cpart)[(int64_t)rb * p.ncol + c] = a;
+    for (int m = 16; m >= 1; m >>= 1) a = cadd(a, dshfl(a, m));
+  }
+  if (lane == 0) red[half][quarter] = a;
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    const int cc = blockIdx.x * 2 + threadIdx.x;
+    if (cc < nset) {
+      double2 t = red[threadIdx.x][0];
+#pragma unroll
+      for (int q = 1; q < 4; ++q) t = cadd(t, red[threadIdx.x][q]);
+      ((double2*)p.cpart)[(int64_t)rb * p.ncol + cc] = t;
+    }
+  }
 }
 
 // coef[pass][c] = sum_rb cpart[rb][c] (PH: real part only).
@@ -102,57 +119,67 @@ __global__ void k_cgs_coef(const Prob* __restrict__ probs, int ph, int pass, int
   ((double2*)p.coef)[(int64_t)pass * p.ncol + c] = s;
 }
 
-// w[row] -= sum_c V[row, col(c)] coef[pass][c].  grid (ceil(maxNpad/128), nprob).
+// w[row] -= sum_c V[row, col(c)] coef[pass][c].  grid (ceil(maxNpad/32), nprob),
+// 8 warps: lane = row of a 32-row slab, warp w takes the set entries c = w mod 8
+// (four loads in flight each), and the eight partial sums meet in shared
+// memory.  Spreading the columns over warps keeps enough loads in flight when
+// N is only a few hundred slabs.
 template <typename ST>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
 k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
   using R = typename RealOf<ST>::T;
   __shared__ ST cf[2 * MAXM + 1];
+  __shared__ ST red[8][32];
   const Prob& p = probs[blockIdx.y];
   const KState* st = p.st;
   if (!kphase(st, newvec)) return;
+  const int64_t row = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
+  if ((int64_t)blockIdx.x * 32 >= p.Npad) return;     // whole block (Npad is a multiple of 128)
   const int j = st->j;
   const int nset = (j + 1) + (ph ? st->ntw : 0);
   const double2* coef = (const double2*)p.coef + (int64_t)pass * p.ncol;
   for (int c = threadIdx.x; c < nset; c += blockDim.x) cf[c] = ccvt<ST>(coef[c]);
   __syncthreads();
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= p.Npad) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const ST* V = (const ST*)p.V;
-  // four independent accumulators keep four column loads in flight per thread
-  ST acc[4] = {czero<ST>(), czero<ST>(), czero<ST>(), czero<ST>()};
   const int nj = j + 1;                     // basis columns [0, j], then the twins
-  if (ph) {
-    const ST* tw = V + (int64_t)(p.ncv + 1) * p.Npad + row;
-    const ST* vb = V + row;
-    int c = 0;
-    for (; c + 4 <= nset; c += 4) {
+  const ST* vb = V + row;
+  const ST* tw = V + (int64_t)(p.ncv + 1) * p.Npad + row;
+  ST acc[4] = {czero<ST>(), czero<ST>(), czero<ST>(), czero<ST>()};
+  int c = warp;
+  for (; c + 24 < nset; c += 32) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int cc = c + u;
-        const ST v = __ldg((cc < nj ? vb + (int64_t)cc * p.Npad : tw + (int64_t)(cc - nj) * p.Npad));
+    for (int u = 0; u < 4; ++u) {
+      const int cc = c + 8 * u;
+      const ST v = __ldg(cc < nj ? vb + (int64_t)cc * p.Npad : tw + (int64_t)(cc - nj) * p.Npad);
+      if (ph) {
         const R f = cf[cc].x;
         acc[u].x = fma(v.x, f, acc[u].x);
         acc[u].y = fma(v.y, f, acc[u].y);
+      } else {
+        cfma(acc[u], v, cf[cc]);
       }
     }
-    for (; c < nset; ++c) {
-      const ST v = __ldg((c < nj ? vb + (int64_t)c * p.Npad : tw + (int64_t)(c - nj) * p.Npad));
+  }
+  for (; c < nset; c += 8) {
+    const ST v = __ldg(c < nj ? vb + (int64_t)c * p.Npad : tw + (int64_t)(c - nj) * p.Npad);
+    if (ph) {
       const R f = cf[c].x;
       acc[0].x = fma(v.x, f, acc[0].x);
       acc[0].y = fma(v.y, f, acc[0].y);
+    } else {
+      cfma(acc[0], v, cf[c]);
     }
-  } else {
-    int c = 0;
-    for (; c + 4 <= nset; c += 4) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) cfma(acc[u], __ldg(V + (int64_t)(c + u) * p.Npad + row), cf[c + u]);
-    }
-    for (; c < nset; ++c) cfma(acc[0], __ldg(V + (int64_t)c * p.Npad + row), cf[c]);
   }
-  const ST tot = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
-  ST* w = (ST*)p.w;
-  w[row] = csub(w[row], tot);
+  red[warp][lane] = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+  __syncthreads();
+  if (warp == 0) {
+    ST tot = red[0][lane];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) tot = cadd(tot, red[q][lane]);
+    ST* w = (ST*)p.w;
+    w[row] = csub(w[row], tot);
+  }
 }
 
 // ---------------------------------------------------------------- norms
@@ -438,9 +465,9 @@ void launch_step_cgs(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t 
   count_launch(3);
   const int newvec = pass >= 2 ? 1 : 0;
   const int ps = pass & 1;
-  k_cgs_dot<ST><<<dim3((ncol + 7) / 8, maxnrb, nprob), 256, 0, s>>>(dprobs, ph, newvec);
+  k_cgs_dot<ST><<<dim3((ncol + 1) / 2, maxnrb, nprob), 256, 0, s>>>(dprobs, ph, newvec);
   k_cgs_coef<<<dim3((ncol + 255) / 256, nprob), 256, 0, s>>>(dprobs, ph, ps, newvec);
-  k_cgs_update<ST><<<dim3((unsigned)((maxNpad + 127) / 128), nprob), 128, 0, s>>>(dprobs, ph, ps, newvec);
+  k_cgs_update<ST><<<dim3((unsigned)((maxNpad + 31) / 32), nprob), 256, 0, s>>>(dprobs, ph, ps, newvec);
 }
 
 template <typename ST>

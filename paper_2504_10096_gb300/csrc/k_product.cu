@@ -13,6 +13,8 @@
 //
 // k_prod_rowblock is the wide-block variant (k columns, GEMM-like): one CTA
 // owns an output block row and reads tile (I,J) or the transpose of (J,I).
+#include <type_traits>
+
 #include "bse_internal.cuh"
 
 namespace bse {
@@ -26,6 +28,14 @@ __device__ __forceinline__ T shfl_xor_c(T v, int m) {
   v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
   v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
   return v;
+}
+
+// (P, Q) = (A + B, A - B) -> (A, B)
+template <typename CT>
+__device__ __forceinline__ void unpack_pq(CT& a, CT& b) {
+  const CT pv = a, qv = b;
+  a.x = 0.5 * (pv.x + qv.x); a.y = 0.5 * (pv.y + qv.y);
+  b.x = 0.5 * (pv.x - qv.x); b.y = 0.5 * (pv.y - qv.y);
 }
 
 // Resolve the input / output vectors of a product for problem p.
@@ -57,40 +67,47 @@ __device__ __forceinline__ bool prod_operands(const Prob& p, int mode, const Gen
   return false;
 }
 
-// One CTA processes a contiguous chunk of tiles of the global job list.
+// A CTA walks the global job list either as one contiguous run or with stride
+// gridDim.x (ProdShape).  Registers allow one FP64 CTA per SM (FP64-pipe
+// bound) and two FP32 ones, so that twice as many tile loads are in flight
+// (the FP32 product is HBM-latency bound).
 template <typename ST, typename R, bool HASB>
-__global__ void __launch_bounds__(PROD_THREADS, 1)
+__global__ void __launch_bounds__(PROD_THREADS, sizeof(R) == 4 ? 2 : 1)
 k_prod_tiles(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs, int njobs,
-             int mode, GenericIO io) {
+             int mode, GenericIO io, int strided) {
   using CT = typename Acc<R>::T;
-  __shared__ CT xc[2][TS];   // column block J: x, s*conj(x)
-  __shared__ CT xr[2][TS];   // row block I
+  // complex128 PH tiles hold P = A + B and Q = A - B; complex64 PH tiles hold A and B
+  constexpr bool PQ = HASB && std::is_same<ST, double2>::value;
+  __shared__ CT xc[TS];      // column block J of x
+  __shared__ CT xr[TS];      // row block I of x
   __shared__ CT red[8][TS];  // column reduction across warps
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int lane = tid & 31, warp = tid >> 5;
-  const int per = (njobs + gridDim.x - 1) / gridDim.x;
-  const int t0 = blockIdx.x * per;
-  const int t1 = min(njobs, t0 + per);
-  for (int t = t0; t < t1; ++t) {
+  const int per = strided ? 1 : (njobs + gridDim.x - 1) / gridDim.x;
+  const int t0 = strided ? blockIdx.x : blockIdx.x * per;
+  const int t1 = strided ? njobs : min(njobs, t0 + per);
+  const int dt = strided ? gridDim.x : 1;
+  for (int t = t0; t < t1; t += dt) {
     const TileJob jb = jobs[t];
     const Prob& p = probs[jb.prob];
     const ST* x; ST* yout; R sB;
     if (!prod_operands<ST, R>(p, mode, io, x, yout, sB)) continue;   // uniform per CTA
     const bool diag = (jb.I == jb.J);
     __syncthreads();                       // smem of the previous tile is free
-    if (tid < TS) {
-      CT a = ccvt<CT>(x[(int64_t)jb.J * TS + tid]);
-      xc[0][tid] = a;
-      xc[1][tid] = cscale(conjc(a), sB);
-    } else {
-      const int r = tid - TS;
-      CT a = ccvt<CT>(x[(int64_t)jb.I * TS + r]);
-      xr[0][r] = a;
-      xr[1][r] = cscale(conjc(a), sB);
-    }
+    if (tid < TS) xc[tid] = ccvt<CT>(x[(int64_t)jb.J * TS + tid]);
+    else xr[tid - TS] = ccvt<CT>(x[(int64_t)jb.I * TS + tid - TS]);
     __syncthreads();
-    const ST* At = (const ST*)p.A + (int64_t)jb.t * (TS * TS);
-    const ST* Bt = HASB ? (const ST*)p.B + (int64_t)jb.t * (TS * TS) : nullptr;
+    // PH: M_s u = A u + s B conj(u) is real-linear; in (Re, Im) form its block
+    // row is [[U_re, -V_im], [U_im, V_re]] with U = A + s B, V = A - s B (the
+    // real matrix M_r of Eq. 5 for s = +1), and the transpose use of the same
+    // tile is [[U_re, U_im], [-V_im, V_re]].  That is 8 real FMAs per stored
+    // element pair instead of the 16 of A u + s B conj(u) as two complex
+    // products.  Complex128 tiles store P = A + B and Q = A - B, so U, V are
+    // P, Q (s = +1) or Q, P (s = -1); complex64 tiles keep A and B exact and
+    // form U, V in registers.
+    const bool pos = sB > (R)0;
+    const ST* At = (const ST*)(PQ && !pos ? p.B : p.A) + (int64_t)jb.t * (TS * TS);
+    const ST* Bt = HASB ? (const ST*)(PQ && !pos ? p.A : p.B) + (int64_t)jb.t * (TS * TS) : nullptr;
     CT racc[8], cacc[8];
 #pragma unroll
     for (int b = 0; b < 8; ++b) cacc[b] = czero<CT>();
@@ -104,18 +121,31 @@ k_prod_tiles(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs, i
         if (HASB) bv[b] = __ldg(Bt + r * TS + tx + 16 * b);
       }
       CT ra = czero<CT>();
-      const CT xra = xr[0][r];
-      const CT xrb = xr[1][r];
+      const CT y = xr[r];
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
         const int c = tx + 16 * b;
-        const CT A = ccvt<CT>(av[b]);
-        cfma(ra, A, xc[0][c]);               // (A_IJ x_J)_r
-        if (!diag) cfmac(cacc[b], A, xra);   // (A_IJ^H x_I)_c
+        const CT xv = xc[c];
         if (HASB) {
-          const CT Bv = ccvt<CT>(bv[b]);
-          cfma(ra, Bv, xc[1][c]);            // s (B_IJ conj x_J)_r
-          if (!diag) cfma(cacc[b], Bv, xrb); // s (B_IJ^T conj x_I)_c
+          CT u, v;
+          if constexpr (PQ) {
+            u = ccvt<CT>(av[b]);
+            v = ccvt<CT>(bv[b]);
+          } else {
+            const CT a0 = ccvt<CT>(av[b]), b0 = ccvt<CT>(bv[b]);
+            u.x = fma(sB, b0.x, a0.x); u.y = fma(sB, b0.y, a0.y);
+            v.x = fma(-sB, b0.x, a0.x); v.y = fma(-sB, b0.y, a0.y);
+          }
+          ra.x = fma(u.x, xv.x, ra.x); ra.x = fma(-v.y, xv.y, ra.x);    // (M_s x_J)_r
+          ra.y = fma(u.y, xv.x, ra.y); ra.y = fma(v.x, xv.y, ra.y);
+          if (!diag) {                                                  // (M_s^T x_I)_c
+            cacc[b].x = fma(u.x, y.x, cacc[b].x); cacc[b].x = fma(u.y, y.y, cacc[b].x);
+            cacc[b].y = fma(v.x, y.y, cacc[b].y); cacc[b].y = fma(-v.y, y.x, cacc[b].y);
+          }
+        } else {
+          const CT A = ccvt<CT>(av[b]);
+          cfma(ra, A, xv);                      // (A_IJ x_J)_r
+          if (!diag) cfmac(cacc[b], A, y);      // (A_IJ^H x_I)_c
         }
       }
       racc[a] = ra;
@@ -207,6 +237,7 @@ k_prod_rowblock(const Prob* __restrict__ probs, int prob, const typename Acc<R>:
                 const typename Acc<R>::T* __restrict__ xb, int ldx, R sB,
                 typename Acc<R>::T* __restrict__ y, int ldy, int K) {
   using CT = typename Acc<R>::T;
+  constexpr bool PQ = HASB && std::is_same<ST, double2>::value;   // tiles hold A + B, A - B
   extern __shared__ unsigned char smem_raw[];
   CT* sA = (CT*)smem_raw;                 // [RB_Q][TS]
   CT* sB_ = sA + RB_Q * TS;               // [RB_Q][TS]
@@ -232,15 +263,21 @@ k_prod_rowblock(const Prob* __restrict__ probs, int prob, const typename Acc<R>:
         // Ablk[r][q] = tile[r][q]
         for (int e = tid; e < TS * RB_Q; e += 256) {
           const int qq = e & (RB_Q - 1), r = e >> 4;
-          sA[qq * TS + r] = ccvt<CT>(At[r * TS + q0 + qq]);
-          if (HASB) sB_[qq * TS + r] = ccvt<CT>(Bt[r * TS + q0 + qq]);
+          CT a = ccvt<CT>(At[r * TS + q0 + qq]), b;
+          if (HASB) b = ccvt<CT>(Bt[r * TS + q0 + qq]);
+          if constexpr (PQ) unpack_pq(a, b);
+          sA[qq * TS + r] = a;
+          if (HASB) sB_[qq * TS + r] = b;
         }
       } else {
         // Ablk[r][q] = conj(tile[q][r]); Bblk[r][q] = tile[q][r]
         for (int e = tid; e < TS * RB_Q; e += 256) {
           const int r = e & (TS - 1), qq = e >> 7;
-          sA[qq * TS + r] = conjc(ccvt<CT>(At[(q0 + qq) * TS + r]));
-          if (HASB) sB_[qq * TS + r] = ccvt<CT>(Bt[(q0 + qq) * TS + r]);
+          CT a = ccvt<CT>(At[(q0 + qq) * TS + r]), b;
+          if (HASB) b = ccvt<CT>(Bt[(q0 + qq) * TS + r]);
+          if constexpr (PQ) unpack_pq(a, b);
+          sA[qq * TS + r] = conjc(a);
+          if (HASB) sB_[qq * TS + r] = b;
         }
       }
       {
@@ -310,6 +347,20 @@ void launch_pack_row(const TIn* rows, int64_t N, int nT, int I, int herm, TSt* d
 template void launch_pack_row<double2, double2>(const double2*, int64_t, int, int, int, double2*, cudaStream_t);
 template void launch_pack_row<float2, float2>(const float2*, int64_t, int, int, int, float2*, cudaStream_t);
 
+// complex128 PH tiles: (A, B) -> (P, Q) = (A + B, A - B), element by element
+__global__ void k_pq_combine(double2* __restrict__ a, double2* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 x = a[i], y = b[i];
+    a[i] = make_double2(x.x + y.x, x.y + y.y);
+    b[i] = make_double2(x.x - y.x, x.y - y.y);
+  }
+}
+
+void launch_pq_combine(double2* a, double2* b, int64_t n, cudaStream_t s) {
+  count_launch();
+  k_pq_combine<<<1024, 256, 0, s>>>(a, b, n);
+}
+
 // ---------------------------------------------------------------- launchers
 static int g_num_sms = 0;
 static int num_sms() {
@@ -322,32 +373,43 @@ static int num_sms() {
   return g_num_sms;
 }
 
+int product_grid(int occ, ProdShape shape, int njobs) {
+  int64_t grid;
+  if (shape.ctas_per_sm < 0) grid = njobs;                       // one CTA per tile
+  else grid = (int64_t)(shape.ctas_per_sm == 0 || shape.ctas_per_sm > occ ? occ : shape.ctas_per_sm) * num_sms();
+  if (grid > njobs) grid = njobs;
+  if (grid < 1) grid = 1;
+  return (int)grid;
+}
+
 template <typename ST, typename R>
-void launch_product(const Prob* dprobs, const TileJob* jobs, int njobs, int nprob, int maxnT,
-                    int mode, int K, const GenericIO* io_host, bool hasB, cudaStream_t s) {
-  count_launch(2);
-  GenericIO io{};
-  if (io_host) io = *io_host;
-  (void)K;
-  // one wave: as many CTAs as can be resident at once (registers bound the
-  // FP64 variant to one CTA per SM), each streaming a contiguous run of tiles
-  static int occ[2][2] = {{0, 0}, {0, 0}};
-  const int ib = hasB ? 1 : 0, ir = sizeof(R) == 8 ? 1 : 0;
-  if (!occ[ib][ir]) {
+int product_occupancy(bool hasB) {
+  static int occ[2] = {0, 0};
+  const int ib = hasB ? 1 : 0;
+  if (!occ[ib]) {
     int o = 0;
     if (hasB)
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_prod_tiles<ST, R, true>, PROD_THREADS, 0);
     else
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_prod_tiles<ST, R, false>, PROD_THREADS, 0);
-    occ[ib][ir] = o > 0 ? o : 1;
+    occ[ib] = o > 0 ? o : 1;
   }
-  int grid = occ[ib][ir] * num_sms();
-  if (grid > njobs) grid = njobs;
-  if (grid < 1) grid = 1;
+  return occ[ib];
+}
+
+template <typename ST, typename R>
+void launch_product(const Prob* dprobs, const TileJob* jobs, int njobs, int nprob, int maxnT,
+                    int mode, int K, const GenericIO* io_host, bool hasB, ProdShape shape, cudaStream_t s) {
+  count_launch(2);
+  GenericIO io{};
+  if (io_host) io = *io_host;
+  (void)K;
+  // registers bound the FP64 variant to one CTA per SM and the FP32 one to two
+  const int grid = product_grid(product_occupancy<ST, R>(hasB), shape, njobs);
   if (hasB)
-    k_prod_tiles<ST, R, true><<<grid, PROD_THREADS, 0, s>>>(dprobs, jobs, njobs, mode, io);
+    k_prod_tiles<ST, R, true><<<grid, PROD_THREADS, 0, s>>>(dprobs, jobs, njobs, mode, io, shape.strided);
   else
-    k_prod_tiles<ST, R, false><<<grid, PROD_THREADS, 0, s>>>(dprobs, jobs, njobs, mode, io);
+    k_prod_tiles<ST, R, false><<<grid, PROD_THREADS, 0, s>>>(dprobs, jobs, njobs, mode, io, shape.strided);
   k_prod_reduce<ST, R><<<dim3(maxnT, nprob), 256, 0, s>>>(dprobs, mode, io);
 }
 
@@ -356,9 +418,11 @@ void launch_prod_reduce_d(const Prob* dprobs, int nprob, int maxnT, int mode, Ge
 }
 
 template void launch_product<double2, double>(const Prob*, const TileJob*, int, int, int, int, int,
-                                              const GenericIO*, bool, cudaStream_t);
+                                              const GenericIO*, bool, ProdShape, cudaStream_t);
 template void launch_product<float2, float>(const Prob*, const TileJob*, int, int, int, int, int,
-                                            const GenericIO*, bool, cudaStream_t);
+                                            const GenericIO*, bool, ProdShape, cudaStream_t);
+template int product_occupancy<double2, double>(bool);
+template int product_occupancy<float2, float>(bool);
 
 template <typename ST, typename R>
 void launch_rowblock(const Prob* dprobs, int prob, int nT, const void* xa, const void* xb, int ldx,

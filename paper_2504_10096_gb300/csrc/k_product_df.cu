@@ -56,10 +56,14 @@ __device__ __forceinline__ void dfc_fmac(DFC& y, float4 a, float4 x) {
   df_acc<LO>(y.ih, y.il, -a.y, -a.w, x.x, x.z);
 }
 
-__device__ __forceinline__ float4 ld_tile(const float4* p) { return __ldg(p); }
-__device__ __forceinline__ float4 ld_tile(const float2* p) {
-  const float2 v = __ldg(p);
-  return make_float4(v.x, v.y, 0.f, 0.f);
+__device__ __forceinline__ float4 widen(float4 v) { return v; }
+__device__ __forceinline__ float4 widen(float2 v) { return make_float4(v.x, v.y, 0.f, 0.f); }
+
+// Knuth's TwoSum: s + e = a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
 }
 
 __device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl) {
@@ -122,18 +126,19 @@ __device__ __forceinline__ bool df_operands(const Prob& p, int mode, const Gener
 template <bool HASB, bool SPLIT>
 __global__ void __launch_bounds__(PROD_THREADS, 2)
 k_prod_tiles_df(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs, int njobs, int mode,
-                GenericIO io) {
-  __shared__ float4 xc[2][TS], xr[2][TS];
+                GenericIO io, int strided) {
+  __shared__ float4 xc[TS], xr[TS];
   // per-thread row partial sums (own slots only); after a barrier the same
   // storage holds the cross-warp column reduction
   __shared__ DFC rpark[8][PROD_THREADS];
   DFC(*red)[TS] = reinterpret_cast<DFC(*)[TS]>(&rpark[0][0]);
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int lane = tid & 31, warp = tid >> 5;
-  const int per = (njobs + gridDim.x - 1) / gridDim.x;
-  const int t0 = blockIdx.x * per;
-  const int t1 = min(njobs, t0 + per);
-  for (int t = t0; t < t1; ++t) {
+  const int per = strided ? 1 : (njobs + gridDim.x - 1) / gridDim.x;
+  const int t0 = strided ? blockIdx.x : blockIdx.x * per;
+  const int t1 = strided ? njobs : min(njobs, t0 + per);
+  const int dt = strided ? gridDim.x : 1;
+  for (int t = t0; t < t1; t += dt) {
     const TileJob jb = jobs[t];
     const Prob& p = probs[jb.prob];
     const double2* x;
@@ -144,14 +149,14 @@ k_prod_tiles_df(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
     {
       const int r = tid & (TS - 1);
       const double2 a = x[(int64_t)(tid < TS ? jb.J : jb.I) * TS + r];
-      const double2 b = make_double2(sB * a.x, -sB * a.y);      // s conj(x)
-      if (tid < TS) { xc[0][r] = split_d(a); xc[1][r] = split_d(b); }
-      else { xr[0][r] = split_d(a); xr[1][r] = split_d(b); }
+      if (tid < TS) xc[r] = split_d(a);
+      else xr[r] = split_d(a);
     }
     __syncthreads();
     using TT = typename std::conditional<SPLIT, float4, float2>::type;
-    const TT* At = (const TT*)(SPLIT ? p.Ahl : p.A) + (int64_t)jb.t * (TS * TS);
-    const TT* Bt = HASB ? (const TT*)(SPLIT ? p.Bhl : p.B) + (int64_t)jb.t * (TS * TS) : nullptr;
+    const bool swap = SPLIT && HASB && sB < 0.0;      // split tiles hold P, Q: U, V = Q, P for s = -1
+    const TT* At = (const TT*)(SPLIT ? (swap ? p.Bhl : p.Ahl) : p.A) + (int64_t)jb.t * (TS * TS);
+    const TT* Bt = HASB ? (const TT*)(SPLIT ? (swap ? p.Ahl : p.Bhl) : p.B) + (int64_t)jb.t * (TS * TS) : nullptr;
     DFC racc[8], cacc[8];
 #pragma unroll
     for (int b = 0; b < 8; ++b) cacc[b] = dfc_zero();
@@ -159,28 +164,80 @@ k_prod_tiles_df(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
     // 8 elements about 1.4k instructions, and a fully unrolled tile would not
     // fit the instruction cache.  Each row's partial sum is parked in shared
     // memory and read back for the cross-lane reduction.
+    // complex64 tiles: the next row's elements are loaded before this row is
+    // processed, so that their latency hides behind ~1.4k instructions of
+    // arithmetic (the split float4 tiles have no registers left for that)
+    constexpr bool PF = !SPLIT;
+    TT av[8], bv[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      av[b] = __ldg(At + ty * TS + tx + 16 * b);
+      if (HASB) bv[b] = __ldg(Bt + ty * TS + tx + 16 * b);
+    }
 #pragma unroll 1
     for (int a = 0; a < 8; ++a) {
       const int r = ty + 16 * a;
-      float4 av[8], bv[8];
+      TT an[8], bn[8];
+      if (PF) {
+        if (a < 7) {
 #pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        av[b] = ld_tile(At + r * TS + tx + 16 * b);
-        if (HASB) bv[b] = ld_tile(Bt + r * TS + tx + 16 * b);
+          for (int b = 0; b < 8; ++b) {
+            an[b] = __ldg(At + (r + 16) * TS + tx + 16 * b);
+            if (HASB) bn[b] = __ldg(Bt + (r + 16) * TS + tx + 16 * b);
+          }
+        }
+      } else if (a > 0) {
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          av[b] = __ldg(At + r * TS + tx + 16 * b);
+          if (HASB) bv[b] = __ldg(Bt + r * TS + tx + 16 * b);
+        }
       }
       DFC ra = dfc_zero();
-      const float4 xra = xr[0][r], xrb = xr[1][r];
+      const float4 y = xr[r];
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
         const int c = tx + 16 * b;
-        dfc_fma<SPLIT>(ra, av[b], xc[0][c]);
-        if (!diag) dfc_fmac<SPLIT>(cacc[b], av[b], xra);
+        const float4 x = xc[c];
         if (HASB) {
-          dfc_fma<SPLIT>(ra, bv[b], xc[1][c]);
-          if (!diag) dfc_fma<SPLIT>(cacc[b], bv[b], xrb);
+          // U = A + s B, V = A - s B: the real block row [[U_re, -V_im], [U_im, V_re]]
+          // of M_s (Eq. 5 for s = +1) and its transpose, 8 multiply-accumulates
+          float4 u, v;
+          if constexpr (SPLIT) {           // split P = A + B, Q = A - B, chosen by pointer
+            u = widen(av[b]);
+            v = widen(bv[b]);
+          } else {                         // exact complex64 A, B: TwoSum gives U, V exactly
+            const float4 a0 = widen(av[b]), b0 = widen(bv[b]);
+            const float sb = sB > 0.0 ? b0.x : -b0.x, sbi = sB > 0.0 ? b0.y : -b0.y;
+            two_sum(a0.x, sb, u.x, u.z);
+            two_sum(a0.y, sbi, u.y, u.w);
+            two_sum(a0.x, -sb, v.x, v.z);
+            two_sum(a0.y, -sbi, v.y, v.w);
+          }
+          df_acc<true>(ra.rh, ra.rl, u.x, u.z, x.x, x.z);
+          df_acc<true>(ra.rh, ra.rl, -v.y, -v.w, x.y, x.w);
+          df_acc<true>(ra.ih, ra.il, u.y, u.w, x.x, x.z);
+          df_acc<true>(ra.ih, ra.il, v.x, v.z, x.y, x.w);
+          if (!diag) {
+            df_acc<true>(cacc[b].rh, cacc[b].rl, u.x, u.z, y.x, y.z);
+            df_acc<true>(cacc[b].rh, cacc[b].rl, u.y, u.w, y.y, y.w);
+            df_acc<true>(cacc[b].ih, cacc[b].il, v.x, v.z, y.y, y.w);
+            df_acc<true>(cacc[b].ih, cacc[b].il, -v.y, -v.w, y.x, y.z);
+          }
+        } else {
+          const float4 aw = widen(av[b]);
+          dfc_fma<SPLIT>(ra, aw, x);
+          if (!diag) dfc_fmac<SPLIT>(cacc[b], aw, y);
         }
       }
       rpark[a][tid] = ra;
+      if (PF) {
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          av[b] = an[b];
+          if (HASB) bv[b] = bn[b];
+        }
+      }
     }
 #pragma unroll
     for (int a = 0; a < 8; ++a) racc[a] = rpark[a][tid];
@@ -233,41 +290,42 @@ __global__ void k_split_tiles(const double2* __restrict__ in, int64_t n, float4*
     out[i] = split_d(in[i]);
 }
 
-int g_sms = 0;
-
 }  // namespace
 
 template <bool HASB, bool SPLIT>
-void launch_df(const Prob* dprobs, const TileJob* jobs, int njobs, int mode, const GenericIO& io, cudaStream_t s) {
+int df_occupancy() {
   static int occ = 0;
-  if (!g_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sms <= 0) g_sms = 1;
-  }
   if (!occ) {
     int o = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_prod_tiles_df<HASB, SPLIT>, PROD_THREADS, 0);
     occ = o > 0 ? o : 1;
   }
-  int grid = occ * g_sms;
-  if (grid > njobs) grid = njobs;
-  if (grid < 1) grid = 1;
-  k_prod_tiles_df<HASB, SPLIT><<<grid, PROD_THREADS, 0, s>>>(dprobs, jobs, njobs, mode, io);
+  return occ;
+}
+
+int product_df_occupancy(bool hasB, bool split) {
+  if (split) return hasB ? df_occupancy<true, true>() : df_occupancy<false, true>();
+  return hasB ? df_occupancy<true, false>() : df_occupancy<false, false>();
+}
+
+template <bool HASB, bool SPLIT>
+void launch_df(const Prob* dprobs, const TileJob* jobs, int njobs, int mode, const GenericIO& io, ProdShape shape,
+               cudaStream_t s) {
+  const int grid = product_grid(df_occupancy<HASB, SPLIT>(), shape, njobs);
+  k_prod_tiles_df<HASB, SPLIT><<<grid, PROD_THREADS, 0, s>>>(dprobs, jobs, njobs, mode, io, shape.strided);
 }
 
 void launch_product_df(const Prob* dprobs, const TileJob* jobs, int njobs, int nprob, int maxnT, int mode,
-                       const GenericIO* io_host, bool hasB, bool split, cudaStream_t s) {
+                       const GenericIO* io_host, bool hasB, bool split, ProdShape shape, cudaStream_t s) {
   count_launch(2);
   GenericIO io{};
   if (io_host) io = *io_host;
   if (split) {
-    if (hasB) launch_df<true, true>(dprobs, jobs, njobs, mode, io, s);
-    else launch_df<false, true>(dprobs, jobs, njobs, mode, io, s);
+    if (hasB) launch_df<true, true>(dprobs, jobs, njobs, mode, io, shape, s);
+    else launch_df<false, true>(dprobs, jobs, njobs, mode, io, shape, s);
   } else {
-    if (hasB) launch_df<true, false>(dprobs, jobs, njobs, mode, io, s);
-    else launch_df<false, false>(dprobs, jobs, njobs, mode, io, s);
+    if (hasB) launch_df<true, false>(dprobs, jobs, njobs, mode, io, shape, s);
+    else launch_df<false, false>(dprobs, jobs, njobs, mode, io, shape, s);
   }
   launch_prod_reduce_d(dprobs, nprob, maxnT, mode, io, s);
 }

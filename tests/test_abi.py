@@ -50,6 +50,10 @@ def test_strerror_and_validation_without_gpu(lib):
     assert lib.bse_destroy(None) == bse.BSE_EINVAL
     assert lib.bse_apply(None, 0, 1, dummy, dummy) == bse.BSE_EINVAL
     assert lib.bse_backward(None, None, 0, None, None) == bse.BSE_EINVAL
+    assert lib.bse_backward_ex(None, None, 0, None, None, 0) == bse.BSE_EINVAL
+    w = (ctypes.c_double * 4)(1.0, 2.0, 3.0, 4.0)
+    out = (ctypes.c_double * 4)()
+    assert lib.bse_haydock(None, dummy, 1, 10, -1, 4, w, 0.1, out, None, None, None) == bse.BSE_EINVAL
 
 
 def test_missing_library_fails_loudly(tmp_path):

@@ -174,3 +174,45 @@ def test_mixed_c64_storage_reaches_fp64_class():
     ov = np.abs(np.einsum("ij,ij->j", Z.conj(), omega_metric_apply(np.vstack([Xo, Yo]))))
     np.testing.assert_allclose(ov, 1.0, atol=1e-6)
     s.close()
+
+
+@pytest.mark.parametrize("form,dtype", [("ph", "c128"), ("tda", "c128"), ("ph", "c64")])
+def test_graph_replay_matches_stream_launches(form, dtype):
+    """The Krylov steps replayed as CUDA graphs run the same kernels in the
+    same order as stream launches: identical eigenvalues, vectors, counters."""
+    A, B = problem(700, dtype, form=form, seed=77)
+    s = _solver(A, B if form == "ph" else None)
+    tol = 1e-12 if dtype == "c128" else 1e-6
+    v1, z1, _ = s.solve(12, tol=tol, graphs=False)
+    st1 = s.stats()
+    v2, z2, _ = s.solve(12, tol=tol, graphs=True)
+    st2 = s.stats()
+    v3, z3, _ = s.solve(12, tol=tol, graphs=True)     # graphs reused from the cache
+    st3 = s.stats()
+    assert np.array_equal(v1, v2) and np.array_equal(v2, v3)
+    assert torch.equal(z1, z2) and torch.equal(z2, z3)
+    for k in ("steps", "passes", "restarts", "launches"):
+        assert st1[k] == st2[k] == st3[k], k
+    assert st2["ms_product"] > 0.0 and st3["ms_product"] > 0.0
+    s.close()
+
+
+def test_product_shape_tuner():
+    """The first solve of a handle times the candidate launch shapes on its
+    own products and keeps the fastest; a second handle of the same kind is
+    tuned from the process cache at creation.  The tile results do not depend
+    on the shape, so both give bit-identical eigenpairs."""
+    A, B = problem(900, "c128", seed=79)
+    s1 = _solver(A, B)
+    v1, z1, _ = s1.solve(10, tol=1e-12)
+    st1 = s1.stats()
+    assert st1["tuned"] == 1
+    assert st1["shape_ctas_per_sm"] >= -1 and st1["shape_strided"] in (0, 1)
+    s2 = _solver(A, B)
+    v2, z2, _ = s2.solve(10, tol=1e-12)
+    st2 = s2.stats()
+    assert st2["tuned"] == 1
+    assert (st2["shape_ctas_per_sm"], st2["shape_strided"]) == (st1["shape_ctas_per_sm"], st1["shape_strided"])
+    assert np.array_equal(v1, v2) and torch.equal(z1, z2)
+    s1.close()
+    s2.close()

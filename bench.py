@@ -346,7 +346,7 @@ def run_product(args):
     from paper_2504_10096_gb300 import bse
     from synthetic import BSEProblemSpec, make_problem
     torch.cuda.set_device(0)
-    N = args.n
+    N = args.n or 8000
     spec = BSEProblemSpec(n=N, n_g=400, seed=1, form="ph", dtype=args.dtype)
     prob = make_problem(spec)          # host generation: no torch.linalg on the device
     stream = torch.cuda.current_stream()
@@ -525,7 +525,7 @@ def run_workload(args):
         A, B = p["A"], p["B"]
         del p
         nev = spec.nev
-        n = args.n if args.n != 8000 else spec.n     # --n shrinks the workload for trial runs
+        n = args.n or spec.n                          # --n shrinks the workload for trial runs
         if n != spec.n:
             A, B = A[:n, :n].contiguous(), B[:n, :n].contiguous()
         out["N"] = n
@@ -565,7 +565,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--mode", default="solve", choices=["solve", "product", "tda", "batch", "adjoint", "mixed",
                                                               "haydock"])
-    ap.add_argument("--n", type=int, default=8000)
+    ap.add_argument("--n", type=int, default=0, help="product mode: N (default 8000); mixed mode: principal "
+                                                       "block of the config-4 matrices (default: all of it)")
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
     ap.add_argument("--op", default="mplus", choices=["mplus", "a"])
     ap.add_argument("--fp64", action="store_true", help="mixed mode: also run the FP64 path")

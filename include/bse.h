@@ -97,8 +97,10 @@ typedef struct bse_solve_opts {
   int ncv;            /* Krylov subspace size m [max(2 nev, nev + 32), <= N] */
   int maxit;          /* limit on Krylov steps [20000]                        */
   uint64_t seed;      /* start vector seed [12345]                            */
-  const void* v0;     /* optional device start vector (N complex, handle
-                         dtype); NULL = counter-based random start            */
+  const void* v0;     /* optional device start vector: N complex values in
+                         the Krylov-basis precision (complex64 for BSE_C64,
+                         complex128 for the other dtypes); single-problem
+                         handles only; NULL = counter-based random start      */
   double lock_tol;    /* Ritz-estimate tolerance used for locking, relative
                          to the Ritz value [tol / 4]                          */
   int stream_launches; /* 0: the Krylov steps of a restart cycle are replayed

@@ -261,14 +261,19 @@ class Solver:
         self.nev = 0
 
     def solve(self, nev, tol=None, ncv=0, maxit=0, seed=0, vectors=True, lock_tol=0.0, check=True,
-              graphs=True):
+              graphs=True, v0=None):
         torch = _torch()
         if tol is None:
             tol = 1e-12 if self.dtype == BSE_C128 else 1e-6
         rows = 2 * self.N if self.form == BSE_PH else self.N
         ev = torch.empty((nev, rows), dtype=self.cdtype, device=self.device) if vectors else None
-        opts = bse_solve_opts(ncv=ncv, maxit=maxit, seed=seed, v0=None, lock_tol=lock_tol,
-                              stream_launches=0 if graphs else 1)
+        v0t = None
+        if v0 is not None:     # start vector in the Krylov-basis precision, on the device
+            torch = _torch()
+            bdt = torch.complex64 if self.dtype == BSE_C64 else torch.complex128
+            v0t = torch.as_tensor(v0).to(device=self.device, dtype=bdt).contiguous()
+        opts = bse_solve_opts(ncv=ncv, maxit=maxit, seed=seed, v0=v0t.data_ptr() if v0t is not None else None,
+                              lock_tol=lock_tol, stream_launches=0 if graphs else 1)
         rc, vals, nconv = bse_solve_ex(self.h, nev, tol, BSE_LOWEST, opts,
                                        ev.data_ptr() if ev is not None else None)
         if check:

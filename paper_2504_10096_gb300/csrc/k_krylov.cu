@@ -121,7 +121,7 @@ __global__ void k_cgs_coef(const Prob* __restrict__ probs, int ph, int pass, int
 
 // w[row] -= sum_c V[row, col(c)] coef[pass][c].  grid (ceil(maxNpad/32), nprob),
 // 8 warps: lane = row of a 32-row slab, warp w takes the set entries c = w mod 8
-// (four loads in flight each), and the eight partial sums meet in shared
+// (eight loads in flight each), and the eight partial sums meet in shared
 // memory.  Spreading the columns over warps keeps enough loads in flight when
 // N is only a few hundred slabs.
 template <typename ST>
@@ -145,11 +145,13 @@ k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
   const int nj = j + 1;                     // basis columns [0, j], then the twins
   const ST* vb = V + row;
   const ST* tw = V + (int64_t)(p.ncv + 1) * p.Npad + row;
-  ST acc[4] = {czero<ST>(), czero<ST>(), czero<ST>(), czero<ST>()};
-  int c = warp;
-  for (; c + 24 < nset; c += 32) {
+  ST acc[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < 8; ++u) acc[u] = czero<ST>();
+  int c = warp;
+  for (; c + 56 < nset; c += 64) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
       const int cc = c + 8 * u;
       const ST v = __ldg(cc < nj ? vb + (int64_t)cc * p.Npad : tw + (int64_t)(cc - nj) * p.Npad);
       if (ph) {
@@ -171,7 +173,8 @@ k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
       cfma(acc[0], v, cf[c]);
     }
   }
-  red[warp][lane] = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+  red[warp][lane] = cadd(cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3])),
+                        cadd(cadd(acc[4], acc[5]), cadd(acc[6], acc[7])));
   __syncthreads();
   if (warp == 0) {
     ST tot = red[0][lane];

@@ -204,24 +204,30 @@ k_prod_tiles(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs, i
 }
 
 // y[I*TS + r] = sum_J part[I][J][r]; grid (maxnT, nprob).
+constexpr int REDUCE_GROUPS = 8;
+
 template <typename ST, typename R>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(REDUCE_GROUPS * TS)
 k_prod_reduce(const Prob* __restrict__ probs, int mode, GenericIO io) {
   using CT = typename Acc<R>::T;
-  __shared__ CT half[TS];
+  __shared__ CT grp[REDUCE_GROUPS - 1][TS];
   const Prob& p = probs[blockIdx.y];
   const int I = blockIdx.x;
   if (I >= p.nT) return;
   const ST* x; ST* y; R sB;
   if (!prod_operands<ST, R>(p, mode, io, x, y, sB)) return;
-  const int r = threadIdx.x & (TS - 1), h = threadIdx.x >> 7;
+  // REDUCE_GROUPS groups of 128 threads sum the slots J = g, g + G, ... in
+  // order; the group sums are then added in group order (fixed rounding order)
+  const int r = threadIdx.x & (TS - 1), g = threadIdx.x >> 7;
   const CT* part = (const CT*)p.part + (int64_t)I * p.nT * TS;
   CT acc = czero<CT>();
-  for (int J = h; J < p.nT; J += 2) acc = cadd(acc, part[(int64_t)J * TS + r]);
-  if (h == 1) half[r] = acc;
+#pragma unroll 4
+  for (int J = g; J < p.nT; J += REDUCE_GROUPS) acc = cadd(acc, part[(int64_t)J * TS + r]);
+  if (g > 0) grp[g - 1][r] = acc;
   __syncthreads();
-  if (h == 0) {
-    acc = cadd(acc, half[r]);
+  if (g == 0) {
+#pragma unroll
+    for (int q = 0; q < REDUCE_GROUPS - 1; ++q) acc = cadd(acc, grp[q][r]);
     y[(int64_t)I * TS + r] = ccvt<ST>(acc);
   }
 }
@@ -410,11 +416,11 @@ void launch_product(const Prob* dprobs, const TileJob* jobs, int njobs, int npro
     k_prod_tiles<ST, R, true><<<grid, PROD_THREADS, 0, s>>>(dprobs, jobs, njobs, mode, io, shape.strided);
   else
     k_prod_tiles<ST, R, false><<<grid, PROD_THREADS, 0, s>>>(dprobs, jobs, njobs, mode, io, shape.strided);
-  k_prod_reduce<ST, R><<<dim3(maxnT, nprob), 256, 0, s>>>(dprobs, mode, io);
+  k_prod_reduce<ST, R><<<dim3(maxnT, nprob), REDUCE_GROUPS * TS, 0, s>>>(dprobs, mode, io);
 }
 
 void launch_prod_reduce_d(const Prob* dprobs, int nprob, int maxnT, int mode, GenericIO io, cudaStream_t s) {
-  k_prod_reduce<double2, double><<<dim3(maxnT, nprob), 256, 0, s>>>(dprobs, mode, io);
+  k_prod_reduce<double2, double><<<dim3(maxnT, nprob), REDUCE_GROUPS * TS, 0, s>>>(dprobs, mode, io);
 }
 
 template void launch_product<double2, double>(const Prob*, const TileJob*, int, int, int, int, int,

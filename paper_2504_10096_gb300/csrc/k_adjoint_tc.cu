@@ -4,15 +4,23 @@
 //     dA = L R_A^H,  dB = L R_B^H      (TDA: L = X g, R_A = X)
 // and, in real arithmetic,  Re(L R^H) = L_re R_re^T + L_im R_im^T,
 //                           Im(L R^H) = L_im R_re^T - L_re R_im^T.
-// One CTA (4 warps) owns a 128 x 128 output tile (I <= J) and keeps its four
-// FP32 accumulators (dA re/im, dB re/im) in the 512 TMEM columns of its SM.
-// Operands are staged in shared memory in the canonical K-major layout
-// without swizzle (8-row x 16-byte core matrices), split into TF32 hi + lo
-// parts (3xTF32: hi*hi + hi*lo + lo*hi, about FP32 accuracy), and one thread
-// issues tcgen05.mma (M = 128, N = 128, K = 8) and commits to an mbarrier.
-// The epilogue reads TMEM with tcgen05.ld and writes the tile and, for I < J,
-// its mirror (dA Hermitian, dB symmetric).  Every wait is bounded; on expiry
-// the CTA records an error, waits again (bounded) and releases its TMEM.
+//
+// k_adj_panels writes the operands once, split into TF32 hi + lo parts (3xTF32:
+// hi*hi + hi*lo + lo*hi, about FP32 accuracy), already in the shared-memory
+// image the tensor cores read: the canonical K-major layout without swizzle
+// (8-row x 16-byte core matrices), in 8 KiB blocks of 128 rows x 16 K.
+//
+// k_adjoint_tc: one CTA (4 warps, one per SM) walks the 128 x 128 output tiles
+// (I <= J) and keeps the four FP32 accumulators (dA re/im, dB re/im) in the
+// 512 TMEM columns of its SM.  Thread 0 runs a two-stage pipeline: a bulk
+// asynchronous copy (cp.async.bulk, completion on an mbarrier) brings the 8 or
+// 12 operand blocks of the next K-chunk while the tensor cores work on the
+// current one (tcgen05.mma M = N = 128, K = 8, committed to a second
+// mbarrier); the first chunk of the next tile is in flight while the four
+// warps drain the accumulators (tcgen05.ld) and write the tile and its mirror
+// (dA Hermitian, dB symmetric).  Every wait is bounded; on expiry the CTA
+// records an error, waits (bounded) for what it has in flight and releases
+// its TMEM, and the host returns a timeout.
 #include <cstdint>
 
 #include "bse_internal.cuh"
@@ -20,26 +28,33 @@
 namespace bse {
 namespace {
 
-constexpr int TCM = 128;         // tile rows (M) and columns (N)
-constexpr int TCKC = 32;         // K elements (tf32) staged per round
+constexpr int TCM = 128;                  // tile rows (M) and columns (N)
+constexpr int KC = 16;                    // K elements per pipeline chunk
 constexpr int TC_THREADS = 128;
-constexpr int OPND = TCM * TCKC * 4;   // bytes of one staged operand (16 KiB)
-constexpr int NOPND = 12;              // L re/im hi/lo (4) + R_A (4) + R_B (4)
+constexpr int BLK = TCM * KC * 4;         // bytes of one operand block (8 KiB)
+constexpr int EPI_BYTES = 4 * 32 * 33 * 8;   // per-warp transpose buffers of the epilogue
 constexpr long long TC_SPIN = 1ll << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// canonical K-major, no swizzle: core matrix (row/8, k/4) at ((row/8)*8 + k/4)*128 bytes;
-// K-direction neighbours 128 B apart (LBO), 8-row groups 1024 B apart (SBO)
+// canonical K-major, no swizzle: core matrix (row/8, k/4) at ((row/8)*4 + k/4)*128 bytes;
+// K-direction neighbours 128 B apart (LBO), 8-row groups 512 B apart (SBO)
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
   d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)((512u >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;   // descriptor version for this architecture
   return d;                 // base offset 0, layout type 0 (no swizzle)
+}
+
+// offset (in floats) of element (row r, K index q) in a panel plane of nk chunks
+__host__ __device__ __forceinline__ int64_t plane_off(int64_t r, int q, int nk) {
+  const int64_t blk = (r >> 7) * nk + (q >> 4);
+  const int ri = (int)(r & 127), ki = q & 15;
+  return blk * (TCM * KC) + (((ri >> 3) * 4 + (ki >> 2)) * 32 + (ri & 7) * 4 + (ki & 3));
 }
 
 __host__ __device__ constexpr uint32_t instr_desc(bool neg_a) {
@@ -61,6 +76,17 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
 }
 
 __device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity) {
@@ -103,133 +129,162 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-// Panels (row-major, ld = kp, rows padded to a multiple of 128, zeros beyond):
-//   P[0] = L_re, P[1] = L_im, P[2] = RA_re, P[3] = RA_im, P[4] = RB_re, P[5] = RB_im
+// Operand planes (rows padded to a multiple of 128, K to a multiple of 16, zeros beyond),
+// each in 8 KiB blocks [row block][K chunk] of the layout plane_off describes:
+//   2j = hi part, 2j + 1 = lo part of  j = 0 L_re, 1 L_im, 2 RA_re, 3 RA_im, 4 RB_re, 5 RB_im
 __global__ void k_adj_panels(const double2* __restrict__ Z, int64_t ldz, int64_t Npad, int64_t N, int k,
-                             const double* __restrict__ g, int ph, int kp, int64_t rows, float* __restrict__ P) {
+                             const double* __restrict__ g, int ph, int nk, int64_t rows, float* __restrict__ P) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   const int kk = ph ? 2 * k : k;
+  const int kp = nk * KC;
   const int64_t plane = rows * kp;
+  const int nj = ph ? 6 : 4;
   for (int q = 0; q < kp; ++q) {
-    float lre = 0.f, lim = 0.f, are = 0.f, aim = 0.f, bre = 0.f, bim = 0.f;
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (r < N && q < kk) {
       const int c = q < k ? q : q - k;
       const double2 x = Z[(int64_t)c * ldz + r];
       const double2 y = ph ? Z[(int64_t)c * ldz + Npad + r] : make_double2(0.0, 0.0);
       const double gc = g[c];
       if (q < k) {               // L = X g, R_A = X, R_B = Y
-        lre = (float)(gc * x.x); lim = (float)(gc * x.y);
-        are = (float)x.x; aim = (float)x.y;
-        bre = (float)y.x; bim = (float)y.y;
+        v[0] = (float)(gc * x.x); v[1] = (float)(gc * x.y);
+        v[2] = (float)x.x; v[3] = (float)x.y;
+        v[4] = (float)y.x; v[5] = (float)y.y;
       } else {                   // L = conj(Y) g, R_A = conj(Y), R_B = conj(X)
-        lre = (float)(gc * y.x); lim = (float)(-gc * y.y);
-        are = (float)y.x; aim = (float)(-y.y);
-        bre = (float)x.x; bim = (float)(-x.y);
+        v[0] = (float)(gc * y.x); v[1] = (float)(-gc * y.y);
+        v[2] = (float)y.x; v[3] = (float)(-y.y);
+        v[4] = (float)x.x; v[5] = (float)(-x.y);
       }
     }
-    const int64_t o = r * kp + q;
-    P[o] = lre; P[plane + o] = lim; P[2 * plane + o] = are; P[3 * plane + o] = aim;
-    P[4 * plane + o] = bre; P[5 * plane + o] = bim;
+    const int64_t o = plane_off(r, q, nk);
+    for (int j = 0; j < nj; ++j) {
+      const float hi = tf32_hi(v[j]);
+      P[(int64_t)(2 * j) * plane + o] = hi;
+      P[(int64_t)(2 * j + 1) * plane + o] = v[j] - hi;
+    }
   }
 }
 
 template <bool PH>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-k_adjoint_tc(const float* __restrict__ P, int64_t rows, int kp, int64_t N, const int2* __restrict__ tiles,
+k_adjoint_tc(const float* __restrict__ P, int64_t rows, int nk, int64_t N, const int2* __restrict__ tiles,
              int ntiles, float2* __restrict__ dA, float2* __restrict__ dB, int* __restrict__ err) {
-  extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ uint64_t mbar;
+  constexpr int NP = PH ? 12 : 8;             // operand blocks per chunk
+  constexpr uint32_t STAGE = NP * BLK;
+  constexpr uint32_t TMEM_COLS = PH ? 512 : 256;
+  extern __shared__ __align__(1024) unsigned char sm[];   // 2 stages, then the epilogue buffers
+  __shared__ uint64_t tma_bar[2], mma_bar[2];
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nop = PH ? NOPND : 8;
-  const int64_t plane = rows * kp;
-  const uint32_t mb = smem_u32(&mbar);
+  const int64_t plane = rows * (int64_t)nk * KC;   // floats per plane
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(512));
+                 "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    for (int s = 0; s < 2; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tma_bar[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar[s])) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tbase = tmem_slot;
-  uint32_t phase = 0;
-  bool ok = true;
+  const uint32_t s0 = smem_u32(sm);
+  float2* buf = reinterpret_cast<float2*>(sm + 2 * STAGE) + warp * (32 * 33);
   const uint32_t id_pos = instr_desc(false), id_neg = instr_desc(true);
-  for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-    const int I = tiles[t].x, J = tiles[t].y;
-    for (int kc = 0; kc < kp && ok; kc += TCKC) {
-      __syncthreads();   // the previous round's MMAs have completed (waited below)
-      // stage: thread tid owns row tid of each operand (A operands: rows of block I, B: block J)
+  // work items: (tile iteration it, chunk c), g = it * nk + c; stage g & 1, phase (g >> 1) & 1
+  const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const long long nitems = (long long)my_tiles * nk;
+  bool ok = true;
+  long long issued = 0, committed = 0;         // thread 0: TMA batches issued, MMA batches committed
+  // TMA batch g: the 8 or 12 operand blocks of chunk g % nk of tile iteration g / nk
+  auto issue_tma = [&](long long g) {
+    const int it = (int)(g / nk), c = (int)(g % nk);
+    const int2 tl = tiles[blockIdx.x + (int64_t)it * gridDim.x];
+    const int s = (int)(g & 1);
+    const uint32_t bar = smem_u32(&tma_bar[s]);
+    mbar_expect_tx(bar, STAGE);
 #pragma unroll 1
-      for (int o = 0; o < nop / 2; ++o) {       // operand o reads panel o
-        const int64_t row = (int64_t)(o < 2 ? I : J) * TCM + tid;
-        const float* pr = P + (int64_t)o * plane + row * kp + kc;
-        unsigned char* hi = sm + (size_t)(2 * o) * OPND;
-        unsigned char* lo = sm + (size_t)(2 * o + 1) * OPND;
-#pragma unroll
-        for (int k4 = 0; k4 < TCKC / 4; ++k4) {
-          const float4 v = *reinterpret_cast<const float4*>(pr + 4 * k4);
-          float4 h, l;
-          h.x = tf32_hi(v.x); h.y = tf32_hi(v.y); h.z = tf32_hi(v.z); h.w = tf32_hi(v.w);
-          l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
-          const int off = ((tid >> 3) * 8 + k4) * 128 + (tid & 7) * 16;
-          *reinterpret_cast<float4*>(hi + off) = h;
-          *reinterpret_cast<float4*>(lo + off) = l;
+    for (int p = 0; p < NP; ++p) {
+      const int rb = p < 4 ? tl.x : tl.y;      // L from block row I, R_A / R_B from block row J
+      const float* src = P + (int64_t)p * plane + ((int64_t)rb * nk + c) * (TCM * KC);
+      bulk_g2s(s0 + (uint32_t)s * STAGE + (uint32_t)p * BLK, src, BLK, bar);
+    }
+  };
+  if (tid == 0 && nitems > 0) {
+    issue_tma(0);
+    issued = 1;
+  }
+  for (int it = 0; it < my_tiles; ++it) {
+    const int2 tl = tiles[blockIdx.x + (int64_t)it * gridDim.x];
+    const int I = tl.x, J = tl.y;
+    const long long g0 = (long long)it * nk;
+    if (tid == 0) {
+      for (int c = 0; c < nk && ok; ++c) {
+        const long long g = g0 + c;
+        const int s = (int)(g & 1);
+        if (!mbar_wait(smem_u32(&tma_bar[s]), (uint32_t)((g >> 1) & 1))) {
+          ok = false;
+          break;
         }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (tid == 0) {
-        const uint32_t s0 = smem_u32(sm);
-        // operand o: hi at 2o, lo at 2o+1; o = 0 L_re, 1 L_im, 2 RA_re, 3 RA_im, 4 RB_re, 5 RB_im
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = s0 + (uint32_t)s * STAGE;
 #pragma unroll 1
-        for (int ks = 0; ks < TCKC / 8; ++ks) {
+        for (int ks = 0; ks < KC / 8; ++ks) {
           const uint32_t koff = (uint32_t)ks * 256u;
-          auto d = [&](int o, int part) { return smem_desc(s0 + (uint32_t)(2 * o + part) * OPND + koff); };
-          const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
+          auto d = [&](int p) { return smem_desc(st + (uint32_t)p * BLK + koff); };
+          const uint32_t first = (c == 0 && ks == 0) ? 0u : 1u;
 #pragma unroll 1
           for (int m = 0; m < (PH ? 2 : 1); ++m) {
-            const int rr = 2 + 2 * m, ri = 3 + 2 * m;       // R_re, R_im operand of this matrix
+            const int rr = 4 + 4 * m, ri = 6 + 4 * m;      // R_re / R_im hi planes of this matrix
             const uint32_t d_re = tbase + (uint32_t)(256 * m), d_im = d_re + 128u;
             // Re += L_re R_re^T + L_im R_im^T   (3xTF32 each)
-            mma_tf32(d_re, d(0, 0), d(rr, 0), id_pos, first);
-            mma_tf32(d_re, d(0, 0), d(rr, 1), id_pos, 1u);
-            mma_tf32(d_re, d(0, 1), d(rr, 0), id_pos, 1u);
-            mma_tf32(d_re, d(1, 0), d(ri, 0), id_pos, 1u);
-            mma_tf32(d_re, d(1, 0), d(ri, 1), id_pos, 1u);
-            mma_tf32(d_re, d(1, 1), d(ri, 0), id_pos, 1u);
+            mma_tf32(d_re, d(0), d(rr), id_pos, first);
+            mma_tf32(d_re, d(0), d(rr + 1), id_pos, 1u);
+            mma_tf32(d_re, d(1), d(rr), id_pos, 1u);
+            mma_tf32(d_re, d(2), d(ri), id_pos, 1u);
+            mma_tf32(d_re, d(2), d(ri + 1), id_pos, 1u);
+            mma_tf32(d_re, d(3), d(ri), id_pos, 1u);
             // Im += L_im R_re^T - L_re R_im^T
-            mma_tf32(d_im, d(1, 0), d(rr, 0), id_pos, first);
-            mma_tf32(d_im, d(1, 0), d(rr, 1), id_pos, 1u);
-            mma_tf32(d_im, d(1, 1), d(rr, 0), id_pos, 1u);
-            mma_tf32(d_im, d(0, 0), d(ri, 0), id_neg, 1u);
-            mma_tf32(d_im, d(0, 0), d(ri, 1), id_neg, 1u);
-            mma_tf32(d_im, d(0, 1), d(ri, 0), id_neg, 1u);
+            mma_tf32(d_im, d(2), d(rr), id_pos, first);
+            mma_tf32(d_im, d(2), d(rr + 1), id_pos, 1u);
+            mma_tf32(d_im, d(3), d(rr), id_pos, 1u);
+            mma_tf32(d_im, d(0), d(ri), id_neg, 1u);
+            mma_tf32(d_im, d(0), d(ri + 1), id_neg, 1u);
+            mma_tf32(d_im, d(1), d(ri), id_neg, 1u);
           }
         }
-        mma_commit(mb);
+        mma_commit(smem_u32(&mma_bar[s]));
+        committed = g + 1;
+        // refill the other stage with batch g + 1 once the MMAs of batch g - 1 have read it
+        if (g + 1 < nitems) {
+          if (g >= 1 && !mbar_wait(smem_u32(&mma_bar[(g + 1) & 1]), (uint32_t)(((g - 1) >> 1) & 1))) {
+            ok = false;
+            break;
+          }
+          issue_tma(g + 1);
+          issued = g + 2;
+        }
       }
-      const int mine = mbar_wait(mb, phase) ? 1 : 0;
-      phase ^= 1u;
-      ok = __syncthreads_and(mine) != 0;   // block-uniform outcome of the bounded wait
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
+    // every thread: the tile's accumulators are final when its last commit has landed
+    const long long gl = g0 + nk - 1;
+    int mine = ok ? 1 : 0;
+    if (mine && !mbar_wait(smem_u32(&mma_bar[gl & 1]), (uint32_t)((gl >> 1) & 1))) mine = 0;
+    ok = __syncthreads_and(mine) != 0;
     if (!ok) break;
-    // epilogue: warp w reads TMEM lanes 32w..32w+31 (tile rows), 32 columns at a
-    // time.  The mirror block is written straight from registers (lanes run
-    // along its rows); the tile itself goes through a per-warp transpose in the
-    // operand shared memory, idle until the next tile's staging, so that lanes
-    // run along its rows too.
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // epilogue: warp w reads TMEM lanes 32w..32w+31 (tile rows), 32 columns at a time.  The
+    // mirror block is written from registers (lanes run along its rows); the tile goes through
+    // a per-warp transpose so that lanes run along its rows too.  A diagonal tile keeps its
+    // upper triangle and mirrors it (dA exactly Hermitian with a real diagonal, dB symmetric).
     const int64_t gi = (int64_t)I * TCM + warp * 32 + lane;
     const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-    float2* buf = reinterpret_cast<float2*>(sm) + warp * (32 * 33);
 #pragma unroll 1
     for (int m = 0; m < (PH ? 2 : 1); ++m) {
       float2* out = m == 0 ? dA : dB;
@@ -238,9 +293,7 @@ k_adjoint_tc(const float* __restrict__ P, int64_t rows, int kp, int64_t N, const
         float re[32], im[32];
         tmem_ld32(tbase + lane_off + (uint32_t)(256 * m + c0), re);
         tmem_ld32(tbase + lane_off + (uint32_t)(256 * m + 128 + c0), im);
-        // a diagonal tile keeps its upper triangle and mirrors it, so dA is
-        // exactly Hermitian (real diagonal: g |x|^2 + g |y|^2) and dB exactly symmetric
-        if (gi < N) {   // mirror: dA Hermitian (conjugate), dB symmetric
+        if (gi < N) {
 #pragma unroll
           for (int q = 0; q < 32; ++q) {
             const int64_t gj = (int64_t)J * TCM + c0 + q;
@@ -263,15 +316,22 @@ k_adjoint_tc(const float* __restrict__ P, int64_t rows, int kp, int64_t N, const
         __syncwarp();
       }
     }
+    // the next tile's first MMA overwrites the accumulators: every read must be done
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
   }
-  if (!ok && tid == 0) atomicExch(err, 1);
-  if (!ok) mbar_wait(mb, phase ^ 1u);   // let an outstanding commit land before releasing TMEM
+  if (!ok && tid == 0) {
+    atomicExch(err, 1);
+    // let what is in flight land before the shared memory and TMEM go away
+    if (issued > 0) mbar_wait(smem_u32(&tma_bar[(issued - 1) & 1]), (uint32_t)(((issued - 1) >> 1) & 1));
+    if (committed > 0)
+      mbar_wait(smem_u32(&mma_bar[(committed - 1) & 1]), (uint32_t)(((committed - 1) >> 1) & 1));
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TMEM_COLS));
 }
 
 int g_tc_sms = 0;
@@ -281,8 +341,8 @@ int g_tc_sms = 0;
 size_t adjoint_tc_panel_bytes(int64_t N, int k, int ph) {
   const int64_t rows = ((N + TCM - 1) / TCM) * TCM;
   const int kk = ph ? 2 * k : k;
-  const int kp = ((kk + TCKC - 1) / TCKC) * TCKC;
-  return (size_t)6 * rows * kp * sizeof(float);
+  const int nk = (kk + KC - 1) / KC;
+  return (size_t)(ph ? 12 : 8) * rows * nk * KC * sizeof(float);
 }
 
 // returns 0 on success, 1 if a bounded wait expired on the device, -1 on a launch error
@@ -291,24 +351,24 @@ int launch_adjoint_tc(const double2* Z, int64_t ldz, int64_t Npad, int64_t N, in
                       cudaStream_t s) {
   const int64_t rows = ((N + TCM - 1) / TCM) * TCM;
   const int kk = ph ? 2 * k : k;
-  const int kp = ((kk + TCKC - 1) / TCKC) * TCKC;
+  const int nk = (kk + KC - 1) / KC;
   count_launch(2);
-  k_adj_panels<<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(Z, ldz, Npad, N, k, g, ph, kp, rows, panels);
+  k_adj_panels<<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(Z, ldz, Npad, N, k, g, ph, nk, rows, panels);
   if (!g_tc_sms) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_tc_sms <= 0) g_tc_sms = 1;
   }
-  const size_t smem = (size_t)(ph ? NOPND : 8) * OPND;
+  const size_t smem = (size_t)2 * (ph ? 12 : 8) * BLK + EPI_BYTES;
   cudaMemsetAsync(derr, 0, sizeof(int), s);
   const int grid = (int)(ntiles < g_tc_sms ? ntiles : g_tc_sms);
   if (ph) {
     cudaFuncSetAttribute(k_adjoint_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_adjoint_tc<true><<<grid, TC_THREADS, smem, s>>>(panels, rows, kp, N, tiles128, (int)ntiles, dA, dB, derr);
+    k_adjoint_tc<true><<<grid, TC_THREADS, smem, s>>>(panels, rows, nk, N, tiles128, (int)ntiles, dA, dB, derr);
   } else {
     cudaFuncSetAttribute(k_adjoint_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_adjoint_tc<false><<<grid, TC_THREADS, smem, s>>>(panels, rows, kp, N, tiles128, (int)ntiles, dA, dB, derr);
+    k_adjoint_tc<false><<<grid, TC_THREADS, smem, s>>>(panels, rows, nk, N, tiles128, (int)ntiles, dA, dB, derr);
   }
   if (cudaGetLastError() != cudaSuccess) return -1;
   int herr = 0;

@@ -486,6 +486,15 @@ def run_workload(args):
                     "adjoint_write_GBs": 2 * spec.n ** 2 * 8 / t_bwd / 1e9,
                     "adjoint_write_frac": 2 * spec.n ** 2 * 8 / t_bwd / 1e9 / _peaks()[0]["hbm_gbs"]})
         s.close(); s64.close()
+    elif args.mode == "profile":
+        # one config-1 solve in a fresh process, nothing else: the command the ncu launch lists run
+        spec = CONFIGS[1]
+        p = make_problem_torch(spec, device="cuda")
+        s = bse.Solver(p["A"], p["B"], stream=stream)
+        vals, _, nconv, t = _timed_solve(s, NEV, TOL, stream, vectors=False)
+        st = s.stats(); s.close()
+        out.update({"workload": "one config-1 solve (PH N=10000 complex128, 100 pairs, FP64)", "s": t,
+                    "krylov_steps": st["steps"], "passes": st["passes"], "launches": st["launches"]})
     elif args.mode == "haydock":
         # Lanczos-Haydock spectrum on the config-1 shapes (PH, N = 10000, complex128)
         spec = CONFIGS[1]
@@ -564,7 +573,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--mode", default="solve", choices=["solve", "product", "tda", "batch", "adjoint", "mixed",
-                                                              "haydock"])
+                                                              "haydock", "profile"])
     ap.add_argument("--n", type=int, default=0, help="product mode: N (default 8000); mixed mode: principal "
                                                        "block of the config-4 matrices (default: all of it)")
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])

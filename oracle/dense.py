@@ -78,7 +78,7 @@ def metric_matrix(A, B):
 
 
 def omega_metric(n):
-    """Omega = diag(I, -I) of Eq. 2 (the survey's and the benchmark spec's J)."""
+    """Omega = diag(I, -I) of Eq. 2 (often written J; the paper's J is the skew matrix of Eq. 4)."""
     return np.diag(np.concatenate([np.ones(n), -np.ones(n)]))
 
 

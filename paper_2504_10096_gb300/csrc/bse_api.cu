@@ -446,13 +446,13 @@ struct Driver {
   int iterate(uint64_t seed, const void* v0) {
     fresh_chain(seed, v0);
     int guard = 0;
-    long long rounds = 0;
+    long long cycles = 0;
     long long maxit = 0;
     for (int i = 0; i < h->count; ++i) maxit = std::max(maxit, h->hstate[i].maxit);
     for (;;) {
-      // every round either adds Krylov steps or restarts; a round without
-      // progress cannot repeat more often than this bound
-      if (++rounds > 4 * maxit + 4096) return BSE_ETIMEOUT;
+      // every pass of this loop either adds Krylov steps or restarts; a pass
+      // without progress cannot repeat more often than this bound
+      if (++cycles > 4 * maxit + 4096) return BSE_ETIMEOUT;
       int rc = read_state();
       if (rc) return rc;
       bool any_active = false, any_bd = false;

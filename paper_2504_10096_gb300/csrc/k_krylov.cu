@@ -72,10 +72,24 @@ k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec) {
     const ST* w = (const ST*)p.w;
     const int64_t r0 = (int64_t)rb * ROWBLK + quarter * (ROWBLK / 4);
     const int64_t r1 = min((int64_t)p.Npad, r0 + ROWBLK / 4);
+    // rounds of 8 rows per lane: all 16 loads of a round are issued before its arithmetic
+    int64_t r = r0 + lane;
     if (ph) {   // K-inner products are real: Re(conj(q) w) only
       R a1 = 0, a2 = 0;   // two chains (x and y products) for more ILP
-#pragma unroll 8
-      for (int64_t r = r0 + lane; r < r1; r += 32) {
+      for (; r + 7 * 32 < r1; r += 8 * 32) {
+        ST q[8], x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          q[u] = __ldg(Q + r + 32 * u);
+          x[u] = __ldg(w + r + 32 * u);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          a1 = fma(q[u].x, x[u].x, a1);
+          a2 = fma(q[u].y, x[u].y, a2);
+        }
+      }
+      for (; r < r1; r += 32) {
         const ST q = __ldg(Q + r), x = __ldg(w + r);
         a1 = fma(q.x, x.x, a1);
         a2 = fma(q.y, x.y, a2);
@@ -83,8 +97,17 @@ k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec) {
       a = mk((double)a1 + (double)a2, 0.0);
     } else {
       ST acc = czero<ST>();
-#pragma unroll 8
-      for (int64_t r = r0 + lane; r < r1; r += 32) cfmac(acc, __ldg(Q + r), __ldg(w + r));
+      for (; r + 7 * 32 < r1; r += 8 * 32) {
+        ST q[8], x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          q[u] = __ldg(Q + r + 32 * u);
+          x[u] = __ldg(w + r + 32 * u);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) cfmac(acc, q[u], x[u]);
+      }
+      for (; r < r1; r += 32) cfmac(acc, __ldg(Q + r), __ldg(w + r));
       a = mk((double)acc.x, (double)acc.y);
     }
 #pragma unroll
@@ -121,11 +144,12 @@ __global__ void k_cgs_coef(const Prob* __restrict__ probs, int ph, int pass, int
 
 // w[row] -= sum_c V[row, col(c)] coef[pass][c].  grid (ceil(maxNpad/32), nprob),
 // 8 warps: lane = row of a 32-row slab, warp w takes the set entries c = w mod 8
-// (eight loads in flight each), and the eight partial sums meet in shared
+// (six or eight loads in flight each), and the eight partial sums meet in shared
 // memory.  Spreading the columns over warps keeps enough loads in flight when
-// N is only a few hundred slabs.
+// N is only a few hundred slabs; three CTAs per SM keep N = 10^4 (316 slabs)
+// in one wave (ncu: at two per SM the last 12 CTAs ran as a second wave).
 template <typename ST>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
   using R = typename RealOf<ST>::T;
   __shared__ ST cf[2 * MAXM + 1];
@@ -145,36 +169,54 @@ k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
   const int nj = j + 1;                     // basis columns [0, j], then the twins
   const ST* vb = V + row;
   const ST* tw = V + (int64_t)(p.ncv + 1) * p.Npad + row;
-  ST acc[8];
-#pragma unroll
-  for (int u = 0; u < 8; ++u) acc[u] = czero<ST>();
+  constexpr int U = sizeof(ST) == 16 ? 6 : 8;   // loads in flight per thread (registers for 3 CTAs/SM)
+  const int64_t ld = p.Npad;
+  auto colptr = [&](int cc) { return cc < nj ? vb + (int64_t)cc * ld : tw + (int64_t)(cc - nj) * ld; };
+  ST part = czero<ST>();
   int c = warp;
-  for (; c + 56 < nset; c += 64) {
+  // all U loads of a round are issued before any of their arithmetic
+  if (ph) {                                 // real coefficients (K-inner products)
+    R ax[U], ay[U];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int cc = c + 8 * u;
-      const ST v = __ldg(cc < nj ? vb + (int64_t)cc * p.Npad : tw + (int64_t)(cc - nj) * p.Npad);
-      if (ph) {
-        const R f = cf[cc].x;
-        acc[u].x = fma(v.x, f, acc[u].x);
-        acc[u].y = fma(v.y, f, acc[u].y);
-      } else {
-        cfma(acc[u], v, cf[cc]);
+    for (int u = 0; u < U; ++u) ax[u] = ay[u] = (R)0;
+    for (; c + 8 * (U - 1) < nset; c += 8 * U) {
+      ST v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = __ldg(colptr(c + 8 * u));
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const R f = cf[c + 8 * u].x;
+        ax[u] = fma(v[u].x, f, ax[u]);
+        ay[u] = fma(v[u].y, f, ay[u]);
       }
     }
-  }
-  for (; c < nset; c += 8) {
-    const ST v = __ldg(c < nj ? vb + (int64_t)c * p.Npad : tw + (int64_t)(c - nj) * p.Npad);
-    if (ph) {
+    for (; c < nset; c += 8) {
+      const ST v = __ldg(colptr(c));
       const R f = cf[c].x;
-      acc[0].x = fma(v.x, f, acc[0].x);
-      acc[0].y = fma(v.y, f, acc[0].y);
-    } else {
-      cfma(acc[0], v, cf[c]);
+      ax[0] = fma(v.x, f, ax[0]);
+      ay[0] = fma(v.y, f, ay[0]);
     }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      part.x += ax[u];
+      part.y += ay[u];
+    }
+  } else {
+    ST acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = czero<ST>();
+    for (; c + 8 * (U - 1) < nset; c += 8 * U) {
+      ST v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = __ldg(colptr(c + 8 * u));
+#pragma unroll
+      for (int u = 0; u < U; ++u) cfma(acc[u], v[u], cf[c + 8 * u]);
+    }
+    for (; c < nset; c += 8) cfma(acc[0], __ldg(colptr(c)), cf[c]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) part = cadd(part, acc[u]);
   }
-  red[warp][lane] = cadd(cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3])),
-                        cadd(cadd(acc[4], acc[5]), cadd(acc[6], acc[7])));
+  red[warp][lane] = part;
   __syncthreads();
   if (warp == 0) {
     ST tot = red[0][lane];

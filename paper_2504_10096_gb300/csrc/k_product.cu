@@ -221,8 +221,15 @@ k_prod_reduce(const Prob* __restrict__ probs, int mode, GenericIO io) {
   const int r = threadIdx.x & (TS - 1), g = threadIdx.x >> 7;
   const CT* part = (const CT*)p.part + (int64_t)I * p.nT * TS;
   CT acc = czero<CT>();
-#pragma unroll 4
-  for (int J = g; J < p.nT; J += REDUCE_GROUPS) acc = cadd(acc, part[(int64_t)J * TS + r]);
+  int J = g;
+  for (; J + 3 * REDUCE_GROUPS < p.nT; J += 4 * REDUCE_GROUPS) {   // four loads in flight, then the sums
+    CT v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = part[(int64_t)(J + u * REDUCE_GROUPS) * TS + r];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc = cadd(acc, v[u]);
+  }
+  for (; J < p.nT; J += REDUCE_GROUPS) acc = cadd(acc, part[(int64_t)J * TS + r]);
   if (g > 0) grp[g - 1][r] = acc;
   __syncthreads();
   if (g == 0) {

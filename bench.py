@@ -451,6 +451,29 @@ def run_workload(args):
                     "passes_total": st["passes"], "launches": st["launches"], "max_residual": st["max_residual"],
                     "product_shape": {"ctas_per_sm": st["shape_ctas_per_sm"], "strided": st["shape_strided"],
                                       "tuned": st["tuned"]}})
+    elif args.mode == "backward":
+        # the config-3 backward alone (complex64 solve, then one tensor-core and one CUDA-core
+        # adjoint): the command the adjoint's ncu capture runs
+        spec = CONFIGS[3]
+        p = make_problem_torch(spec, device="cuda")
+        n = args.n or spec.n                       # --n: a principal block (small ncu captures)
+        s = bse.Solver(p["A"][:n, :n].contiguous(), p["B"][:n, :n].contiguous(), stream=stream)
+        del p
+        vals, _, _, t_solve = _timed_solve(s, spec.nev, 1e-6, stream, vectors=False)
+        g = np.linspace(0.5, 1.5, spec.nev)
+        res = {}
+        for name, impl in (("tensor_cores", bse.BSE_IMPL_TENSOR_CORES), ("cuda_cores", bse.BSE_IMPL_CUDA_CORES)):
+            s.backward(g, impl=impl)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.backward(g, impl=impl)
+            e1.record(stream); torch.cuda.synchronize()
+            res[f"backward_{name}_s"] = e0.elapsed_time(e1) / 1e3
+        s.close()
+        out.update({"workload": f"PH N={n} complex64 nev=50: backward (Hellmann-Feynman adjoint) only",
+                    "solve_s": t_solve, **res,
+                    "write_GBs_tensor_cores": 2 * n ** 2 * 8 / res["backward_tensor_cores_s"] / 1e9})
     elif args.mode == "adjoint":
         spec = CONFIGS[3]
         p = make_problem_torch(spec, device="cuda")
@@ -573,7 +596,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--mode", default="solve", choices=["solve", "product", "tda", "batch", "adjoint", "mixed",
-                                                              "haydock", "profile"])
+                                                              "haydock", "profile", "backward"])
     ap.add_argument("--n", type=int, default=0, help="product mode: N (default 8000); mixed mode: principal "
                                                        "block of the config-4 matrices (default: all of it)")
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])

@@ -10,17 +10,18 @@
 // image the tensor cores read: the canonical K-major layout without swizzle
 // (8-row x 16-byte core matrices), in 8 KiB blocks of 128 rows x 16 K.
 //
-// k_adjoint_tc: one CTA (4 warps, one per SM) walks the 128 x 128 output tiles
-// (I <= J) and keeps the four FP32 accumulators (dA re/im, dB re/im) in the
-// 512 TMEM columns of its SM.  Thread 0 runs a two-stage pipeline: a bulk
-// asynchronous copy (cp.async.bulk, completion on an mbarrier) brings the 8 or
-// 12 operand blocks of the next K-chunk while the tensor cores work on the
-// current one (tcgen05.mma M = N = 128, K = 8, committed to a second
-// mbarrier); the first chunk of the next tile is in flight while the four
-// warps drain the accumulators (tcgen05.ld) and write the tile and its mirror
-// (dA Hermitian, dB symmetric).  Every wait is bounded; on expiry the CTA
-// records an error, waits (bounded) for what it has in flight and releases
-// its TMEM, and the host returns a timeout.
+// k_adjoint_tc: one persistent CTA per SM, warp-specialised.  The work unit is
+// a half-tile (128 output rows x 64 columns of a 128 x 128 tile I <= J), whose
+// FP32 accumulators (dA re/im, dB re/im) take 256 TMEM columns, so two sets
+// fit in the SM's 512: while warps 0-3 drain one set (tcgen05.ld) and write
+// the half-tile and its mirror (dA Hermitian, dB symmetric), warp 4 already
+// runs the next half-tile's tcgen05.mma (M = 128, N = 64, K = 8) into the
+// other.  Warp 4 also feeds a three-stage shared-memory pipeline with bulk
+// asynchronous copies (cp.async.bulk, completion on mbarriers); tcgen05.commit
+// releases a stage when its MMAs finish and publishes a finished accumulator
+// set.  Every wait is bounded; on expiry the CTA records an error, stops, waits
+// (bounded) for what it has in flight and releases its TMEM, and the host
+// returns a timeout.
 #include <cstdint>
 
 #include "bse_internal.cuh"
@@ -30,7 +31,8 @@ namespace {
 
 constexpr int TCM = 128;                  // tile rows (M) and columns (N)
 constexpr int KC = 16;                    // K elements per pipeline chunk
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 160;           // warps 0-3 epilogue, warp 4 copies + MMAs
+constexpr int NSTAGE = 3;                 // shared-memory pipeline stages
 constexpr int BLK = TCM * KC * 4;         // bytes of one operand block (8 KiB)
 constexpr int EPI_BYTES = 4 * 32 * 33 * 8;   // per-warp transpose buffers of the epilogue
 constexpr long long TC_SPIN = 1ll << 26;
@@ -62,7 +64,7 @@ __host__ __device__ constexpr uint32_t instr_desc(bool neg_a) {
          | (2u << 7)                        // A: TF32
          | (2u << 10)                       // B: TF32
          | ((neg_a ? 1u : 0u) << 13)        // negate A
-         | ((uint32_t)(TCM >> 3) << 17)     // N / 8
+         | ((uint32_t)(64 >> 3) << 17)      // N / 8 (half-tile: 64 output columns)
          | ((uint32_t)(TCM >> 4) << 24);    // M / 16   (A and B K-major)
 }
 
@@ -166,16 +168,27 @@ __global__ void k_adj_panels(const double2* __restrict__ Z, int64_t ldz, int64_t
   }
 }
 
+// Half-tile unit h = 2 * (tile iteration) + q: output rows of block I, columns
+// J * 128 + 64 q ... + 63 (M = 128, N = 64), so that two accumulator sets fit
+// in the 512 TMEM columns and the epilogue of one half-tile overlaps the MMAs
+// of the next.  Warps 0-3 drain TMEM and write; warp 4 (one lane) issues the
+// bulk copies and the MMAs.  Barriers: full[s] / empty[s] for the three
+// shared-memory stages (copies landed / MMAs done reading), tfull[b] /
+// tempty[b] for the two accumulator buffers (MMAs done / epilogue done).
 template <bool PH>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_adjoint_tc(const float* __restrict__ P, int64_t rows, int nk, int64_t N, const int2* __restrict__ tiles,
              int ntiles, float2* __restrict__ dA, float2* __restrict__ dB, int* __restrict__ err) {
-  constexpr int NP = PH ? 12 : 8;             // operand blocks per chunk
-  constexpr uint32_t STAGE = NP * BLK;
-  constexpr uint32_t TMEM_COLS = PH ? 512 : 256;
-  extern __shared__ __align__(1024) unsigned char sm[];   // 2 stages, then the epilogue buffers
-  __shared__ uint64_t tma_bar[2], mma_bar[2];
+  constexpr int NR = PH ? 8 : 4;                     // R planes (R_A, and R_B for PH)
+  constexpr uint32_t LBYTES = 4 * BLK;               // L: 4 planes x 128 rows
+  constexpr uint32_t RBLK = BLK / 2;                 // one R plane, 64 rows
+  constexpr uint32_t STAGE = LBYTES + NR * RBLK;
+  constexpr uint32_t ACC = PH ? 256 : 128;           // TMEM columns of one accumulator set
+  constexpr uint32_t TMEM_COLS = 2 * ACC;
+  extern __shared__ __align__(1024) unsigned char sm[];   // NSTAGE stages, then the epilogue buffers
+  __shared__ uint64_t full[NSTAGE], empty[NSTAGE], tfull[2], tempty[2];
   __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t plane = rows * (int64_t)nk * KC;   // floats per plane
   if (warp == 0) {
@@ -184,10 +197,15 @@ k_adjoint_tc(const float* __restrict__ P, int64_t rows, int nk, int64_t N, const
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int s = 0; s < 2; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tma_bar[s])) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar[s])) : "memory");
+    for (int s = 0; s < NSTAGE; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
     }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tfull[b])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tempty[b])), "r"(128) : "memory");
+    }
+    abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -195,137 +213,153 @@ k_adjoint_tc(const float* __restrict__ P, int64_t rows, int nk, int64_t N, const
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tbase = tmem_slot;
   const uint32_t s0 = smem_u32(sm);
-  float2* buf = reinterpret_cast<float2*>(sm + 2 * STAGE) + warp * (32 * 33);
-  const uint32_t id_pos = instr_desc(false), id_neg = instr_desc(true);
-  // work items: (tile iteration it, chunk c), g = it * nk + c; stage g & 1, phase (g >> 1) & 1
   const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  const long long nitems = (long long)my_tiles * nk;
-  bool ok = true;
-  long long issued = 0, committed = 0;         // thread 0: TMA batches issued, MMA batches committed
-  // TMA batch g: the 8 or 12 operand blocks of chunk g % nk of tile iteration g / nk
-  auto issue_tma = [&](long long g) {
-    const int it = (int)(g / nk), c = (int)(g % nk);
-    const int2 tl = tiles[blockIdx.x + (int64_t)it * gridDim.x];
-    const int s = (int)(g & 1);
-    const uint32_t bar = smem_u32(&tma_bar[s]);
-    mbar_expect_tx(bar, STAGE);
+  const int nhalf = 2 * my_tiles;
+  volatile int* vabort = &abort_flag;
+
+  if (warp == 4) {
+    // ------------------------------------------------ copies and MMAs (one lane)
+    if (lane == 0) {
+      const uint32_t idp = instr_desc(false), idn = instr_desc(true);
+      const long long nb = (long long)nhalf * nk;     // batches: (half-tile, K-chunk)
+      auto issue_tma = [&](long long g) {
+        const int h = (int)(g / nk), c = (int)(g % nk);
+        const int2 tl = tiles[blockIdx.x + (int64_t)(h >> 1) * gridDim.x];
+        const int q = h & 1;
+        const int s = (int)(g % NSTAGE);
+        const uint32_t bar = smem_u32(&full[s]);
+        const uint32_t st = s0 + (uint32_t)s * STAGE;
+        mbar_expect_tx(bar, STAGE);
 #pragma unroll 1
-    for (int p = 0; p < NP; ++p) {
-      const int rb = p < 4 ? tl.x : tl.y;      // L from block row I, R_A / R_B from block row J
-      const float* src = P + (int64_t)p * plane + ((int64_t)rb * nk + c) * (TCM * KC);
-      bulk_g2s(s0 + (uint32_t)s * STAGE + (uint32_t)p * BLK, src, BLK, bar);
-    }
-  };
-  if (tid == 0 && nitems > 0) {
-    issue_tma(0);
-    issued = 1;
-  }
-  for (int it = 0; it < my_tiles; ++it) {
-    const int2 tl = tiles[blockIdx.x + (int64_t)it * gridDim.x];
-    const int I = tl.x, J = tl.y;
-    const long long g0 = (long long)it * nk;
-    if (tid == 0) {
-      for (int c = 0; c < nk && ok; ++c) {
-        const long long g = g0 + c;
-        const int s = (int)(g & 1);
-        if (!mbar_wait(smem_u32(&tma_bar[s]), (uint32_t)((g >> 1) & 1))) {
-          ok = false;
-          break;
-        }
+        for (int p = 0; p < 4; ++p)           // L: block row I, all 128 rows
+          bulk_g2s(st + (uint32_t)p * BLK, P + (int64_t)p * plane + ((int64_t)tl.x * nk + c) * (TCM * KC), BLK,
+                   bar);
+#pragma unroll 1
+        for (int p = 0; p < NR; ++p)          // R: block row J, rows 64 q ... 64 q + 63
+          bulk_g2s(st + LBYTES + (uint32_t)p * RBLK,
+                   reinterpret_cast<const char*>(P + (int64_t)(4 + p) * plane + ((int64_t)tl.y * nk + c) * (TCM * KC)) +
+                       q * RBLK,
+                   RBLK, bar);
+      };
+      long long issued = 0, committed = 0;
+      for (; issued < nb && issued < NSTAGE; ++issued) issue_tma(issued);
+      bool ok = true;
+      for (long long g = 0; g < nb && ok; ++g) {
+        const int h = (int)(g / nk), c = (int)(g % nk);
+        const int s = (int)(g % NSTAGE), b = h & 1;
+        if (*vabort) { ok = false; break; }
+        if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((g / NSTAGE) & 1))) { ok = false; break; }
+        if (c == 0 && !mbar_wait(smem_u32(&tempty[b]), (uint32_t)(((h >> 1) & 1) ^ 1))) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st = s0 + (uint32_t)s * STAGE;
 #pragma unroll 1
         for (int ks = 0; ks < KC / 8; ++ks) {
           const uint32_t koff = (uint32_t)ks * 256u;
-          auto d = [&](int p) { return smem_desc(st + (uint32_t)p * BLK + koff); };
+          auto dl = [&](int p) { return smem_desc(st + (uint32_t)p * BLK + koff); };
+          auto dr = [&](int p) { return smem_desc(st + LBYTES + (uint32_t)p * RBLK + koff); };
           const uint32_t first = (c == 0 && ks == 0) ? 0u : 1u;
 #pragma unroll 1
           for (int m = 0; m < (PH ? 2 : 1); ++m) {
-            const int rr = 4 + 4 * m, ri = 6 + 4 * m;      // R_re / R_im hi planes of this matrix
-            const uint32_t d_re = tbase + (uint32_t)(256 * m), d_im = d_re + 128u;
+            const int rr = 4 * m, ri = 4 * m + 2;            // R_re / R_im hi planes of this matrix
+            const uint32_t d_re = tbase + (uint32_t)b * ACC + (uint32_t)(128 * m), d_im = d_re + 64u;
             // Re += L_re R_re^T + L_im R_im^T   (3xTF32 each)
-            mma_tf32(d_re, d(0), d(rr), id_pos, first);
-            mma_tf32(d_re, d(0), d(rr + 1), id_pos, 1u);
-            mma_tf32(d_re, d(1), d(rr), id_pos, 1u);
-            mma_tf32(d_re, d(2), d(ri), id_pos, 1u);
-            mma_tf32(d_re, d(2), d(ri + 1), id_pos, 1u);
-            mma_tf32(d_re, d(3), d(ri), id_pos, 1u);
+            mma_tf32(d_re, dl(0), dr(rr), idp, first);
+            mma_tf32(d_re, dl(0), dr(rr + 1), idp, 1u);
+            mma_tf32(d_re, dl(1), dr(rr), idp, 1u);
+            mma_tf32(d_re, dl(2), dr(ri), idp, 1u);
+            mma_tf32(d_re, dl(2), dr(ri + 1), idp, 1u);
+            mma_tf32(d_re, dl(3), dr(ri), idp, 1u);
             // Im += L_im R_re^T - L_re R_im^T
-            mma_tf32(d_im, d(2), d(rr), id_pos, first);
-            mma_tf32(d_im, d(2), d(rr + 1), id_pos, 1u);
-            mma_tf32(d_im, d(3), d(rr), id_pos, 1u);
-            mma_tf32(d_im, d(0), d(ri), id_neg, 1u);
-            mma_tf32(d_im, d(0), d(ri + 1), id_neg, 1u);
-            mma_tf32(d_im, d(1), d(ri), id_neg, 1u);
+            mma_tf32(d_im, dl(2), dr(rr), idp, first);
+            mma_tf32(d_im, dl(2), dr(rr + 1), idp, 1u);
+            mma_tf32(d_im, dl(3), dr(rr), idp, 1u);
+            mma_tf32(d_im, dl(0), dr(ri), idn, 1u);
+            mma_tf32(d_im, dl(0), dr(ri + 1), idn, 1u);
+            mma_tf32(d_im, dl(1), dr(ri), idn, 1u);
           }
         }
-        mma_commit(smem_u32(&mma_bar[s]));
+        mma_commit(smem_u32(&empty[s]));              // stage s may be refilled once these finish
+        if (c == nk - 1) mma_commit(smem_u32(&tfull[b]));   // the half-tile's accumulators are final
         committed = g + 1;
-        // refill the other stage with batch g + 1 once the MMAs of batch g - 1 have read it
-        if (g + 1 < nitems) {
-          if (g >= 1 && !mbar_wait(smem_u32(&mma_bar[(g + 1) & 1]), (uint32_t)(((g - 1) >> 1) & 1))) {
-            ok = false;
-            break;
-          }
-          issue_tma(g + 1);
-          issued = g + 2;
+        // refill the stage of batch g - 1 (its MMAs finish while batch g's run)
+        if (g >= 1 && issued < nb) {
+          const long long gp = g - 1;
+          if (!mbar_wait(smem_u32(&empty[gp % NSTAGE]), (uint32_t)((gp / NSTAGE) & 1))) { ok = false; break; }
+          issue_tma(issued);
+          ++issued;
         }
       }
+      if (!ok) {
+        *vabort = 1;
+        atomicExch(err, 1);
+      }
+      // nothing may be in flight when the shared memory and TMEM go away
+      if (issued > 0) {
+        const long long gi = issued - 1;
+        mbar_wait(smem_u32(&full[gi % NSTAGE]), (uint32_t)((gi / NSTAGE) & 1));
+      }
+      if (committed > 0) {
+        const long long gc = committed - 1;
+        mbar_wait(smem_u32(&empty[gc % NSTAGE]), (uint32_t)((gc / NSTAGE) & 1));
+      }
     }
-    // every thread: the tile's accumulators are final when its last commit has landed
-    const long long gl = g0 + nk - 1;
-    int mine = ok ? 1 : 0;
-    if (mine && !mbar_wait(smem_u32(&mma_bar[gl & 1]), (uint32_t)((gl >> 1) & 1))) mine = 0;
-    ok = __syncthreads_and(mine) != 0;
-    if (!ok) break;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: warp w reads TMEM lanes 32w..32w+31 (tile rows), 32 columns at a time.  The
-    // mirror block is written from registers (lanes run along its rows); the tile goes through
-    // a per-warp transpose so that lanes run along its rows too.  A diagonal tile keeps its
-    // upper triangle and mirrors it (dA exactly Hermitian with a real diagonal, dB symmetric).
-    const int64_t gi = (int64_t)I * TCM + warp * 32 + lane;
+  } else {
+    // ------------------------------------------------ epilogue (warps 0-3)
+    float2* buf = reinterpret_cast<float2*>(sm + NSTAGE * STAGE) + warp * (32 * 33);
     const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-#pragma unroll 1
-    for (int m = 0; m < (PH ? 2 : 1); ++m) {
-      float2* out = m == 0 ? dA : dB;
-#pragma unroll 1
-      for (int c0 = 0; c0 < TCM; c0 += 32) {
-        float re[32], im[32];
-        tmem_ld32(tbase + lane_off + (uint32_t)(256 * m + c0), re);
-        tmem_ld32(tbase + lane_off + (uint32_t)(256 * m + 128 + c0), im);
-        if (gi < N) {
-#pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            const int64_t gj = (int64_t)J * TCM + c0 + q;
-            if (gj < N && (I != J || gj > gi)) out[gj * N + gi] = make_float2(re[q], m == 0 ? -im[q] : im[q]);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 32; ++q) buf[lane * 33 + q] = make_float2(re[q], im[q]);
-        __syncwarp();
-        const int64_t gj = (int64_t)J * TCM + c0 + lane;
-#pragma unroll 4
-        for (int rr = 0; rr < 32; ++rr) {
-          const int64_t row = (int64_t)I * TCM + warp * 32 + rr;
-          if (row < N && gj < N && (I != J || gj >= row)) {
-            float2 v = buf[rr * 33 + lane];
-            if (m == 0 && gj == row) v.y = 0.f;
-            out[row * N + gj] = v;
-          }
-        }
-        __syncwarp();
+    for (int h = 0; h < nhalf; ++h) {
+      const int b = h & 1;
+      if (*vabort) break;
+      // warp-uniform outcome: tcgen05.ld below needs the whole warp
+      const bool ready = __all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[b]), (uint32_t)((h >> 1) & 1)) ? 1 : 0);
+      if (!ready) {
+        *vabort = 1;
+        atomicExch(err, 1);
+        break;
       }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int2 tl = tiles[blockIdx.x + (int64_t)(h >> 1) * gridDim.x];
+      const int I = tl.x, J = tl.y, q = h & 1;
+      const int64_t gi = (int64_t)I * TCM + warp * 32 + lane;
+      // the mirror block is written from registers (lanes run along its rows); the tile goes
+      // through a per-warp transpose so that lanes run along its rows too.  A diagonal tile keeps
+      // its upper triangle and mirrors it (dA exactly Hermitian with a real diagonal, dB symmetric)
+#pragma unroll 1
+      for (int m = 0; m < (PH ? 2 : 1); ++m) {
+        float2* out = m == 0 ? dA : dB;
+#pragma unroll 1
+        for (int c0 = 0; c0 < 64; c0 += 32) {
+          float re[32], im[32];
+          tmem_ld32(tbase + lane_off + (uint32_t)b * ACC + (uint32_t)(128 * m + c0), re);
+          tmem_ld32(tbase + lane_off + (uint32_t)b * ACC + (uint32_t)(128 * m + 64 + c0), im);
+          const int64_t jb = (int64_t)J * TCM + 64 * q + c0;
+          if (gi < N) {
+#pragma unroll
+            for (int qq = 0; qq < 32; ++qq) {
+              const int64_t gj = jb + qq;
+              if (gj < N && (I != J || gj > gi)) out[gj * N + gi] = make_float2(re[qq], m == 0 ? -im[qq] : im[qq]);
+            }
+          }
+#pragma unroll
+          for (int qq = 0; qq < 32; ++qq) buf[lane * 33 + qq] = make_float2(re[qq], im[qq]);
+          __syncwarp();
+          const int64_t gj = jb + lane;
+#pragma unroll 4
+          for (int rr = 0; rr < 32; ++rr) {
+            const int64_t row = (int64_t)I * TCM + warp * 32 + rr;
+            if (row < N && gj < N && (I != J || gj >= row)) {
+              float2 v = buf[rr * 33 + lane];
+              if (m == 0 && gj == row) v.y = 0.f;
+              out[row * N + gj] = v;
+            }
+          }
+          __syncwarp();
+        }
+      }
+      // this accumulator set may be overwritten by the half-tile after next
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[b])) : "memory");
     }
-    // the next tile's first MMA overwrites the accumulators: every read must be done
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-  }
-  if (!ok && tid == 0) {
-    atomicExch(err, 1);
-    // let what is in flight land before the shared memory and TMEM go away
-    if (issued > 0) mbar_wait(smem_u32(&tma_bar[(issued - 1) & 1]), (uint32_t)(((issued - 1) >> 1) & 1));
-    if (committed > 0)
-      mbar_wait(smem_u32(&mma_bar[(committed - 1) & 1]), (uint32_t)(((committed - 1) >> 1) & 1));
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -360,7 +394,8 @@ int launch_adjoint_tc(const double2* Z, int64_t ldz, int64_t Npad, int64_t N, in
     cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_tc_sms <= 0) g_tc_sms = 1;
   }
-  const size_t smem = (size_t)2 * (ph ? 12 : 8) * BLK + EPI_BYTES;
+  // stage: L (4 planes x 8 KiB) + R (8 or 4 planes x 4 KiB)
+  const size_t smem = (size_t)NSTAGE * (4 * BLK + (ph ? 8 : 4) * (BLK / 2)) + EPI_BYTES;
   cudaMemsetAsync(derr, 0, sizeof(int), s);
   const int grid = (int)(ntiles < g_tc_sms ? ntiles : g_tc_sms);
   if (ph) {

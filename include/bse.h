@@ -311,6 +311,19 @@ int bse_haydock(bse_handle* h, const void* d, int where, int m, int sign,
                 int nw, const double* omega, double eta, double* spectrum_out,
                 double* response_out, double* coef_out, int* steps_out);
 
+/*
+ * bse_selftest_bounded_wait -- exercise the failure path of the device-side
+ * waits (no handle needed).  Every wait of this library's kernels on an
+ * mbarrier (tensor-core pipelines) polls a bounded number of times; on expiry
+ * the kernel records an error, releases what it holds and returns, and the
+ * call reports BSE_ETIMEOUT, leaving the CUDA context usable.  This launches
+ * one such wait on the current device: arrive = 0 waits on a barrier that
+ * nothing completes (*expired = 1 after about 10^6 polls), arrive = 1 completes
+ * it first (*expired = 0).  Returns BSE_EINVAL for bad arguments, BSE_ECUDA on
+ * a CUDA error.  The paper has no counterpart; it is a test of this build.
+ */
+int bse_selftest_bounded_wait(int arrive, int* expired);
+
 /* Counters of the last solve or spectrum (single-problem handles; for
    batched handles the sums over problems). */
 int bse_get_stats(const bse_handle* h, bse_stats* out);

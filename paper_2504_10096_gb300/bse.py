@@ -27,7 +27,7 @@ BSE_OP_A, BSE_OP_MPLUS, BSE_OP_MMINUS, BSE_OP_H = 0, 1, 2, 3
 
 EXPORTED = ["bse_strerror", "bse_create", "bse_create_batched", "bse_solve", "bse_solve_ex",
             "bse_solve_batched", "bse_backward", "bse_apply", "bse_get_stats", "bse_destroy",
-            "bse_apply_noalloc", "bse_backward_ex", "bse_haydock"]
+            "bse_apply_noalloc", "bse_backward_ex", "bse_haydock", "bse_selftest_bounded_wait"]
 BSE_IMPL_AUTO, BSE_IMPL_CUDA_CORES, BSE_IMPL_TENSOR_CORES = 0, 1, 2
 BSE_NOALLOC_MAX_N = 4096
 
@@ -83,6 +83,7 @@ def load_library(path: str | None = None):
     lib.bse_destroy.argtypes = [H]
     lib.bse_apply_noalloc.argtypes = [c_i64, c_vp, c_vp, c_int, c_int, c_vp, c_vp, c_vp]
     lib.bse_backward_ex.argtypes = [H, ctypes.POINTER(c_dbl), c_int, c_vp, c_vp, c_int]
+    lib.bse_selftest_bounded_wait.argtypes = [c_int, ctypes.POINTER(c_int)]
     PD = ctypes.POINTER(c_dbl)
     lib.bse_haydock.argtypes = [H, c_vp, c_int, c_int, c_int, c_int, PD, c_dbl, PD, PD, PD,
                                 ctypes.POINTER(c_int)]
@@ -167,6 +168,13 @@ def bse_haydock(h, d_ptr, where, m, sign, omega, eta, want_coefs=True):
                                     spec.ctypes.data_as(P), resp.ctypes.data_as(P),
                                     coef.ctypes.data_as(P) if coef is not None else None, ctypes.byref(steps))
     return rc, spec, resp[0::2] + 1j * resp[1::2], coef, steps.value
+
+
+def bse_selftest_bounded_wait(arrive):
+    """Returns (status, expired) of one bounded device wait (see bse.h)."""
+    e = ctypes.c_int(-1)
+    rc = load_library().bse_selftest_bounded_wait(int(arrive), ctypes.byref(e))
+    return rc, e.value
 
 
 def bse_apply(h, op, k, X_ptr, Y_ptr):

@@ -1266,6 +1266,11 @@ int bse_haydock(bse_handle* h, const void* d, int where, int m, int sign, int nw
                                steps_out);
 }
 
+int bse_selftest_bounded_wait(int arrive, int* expired) {
+  if (!expired || (arrive != 0 && arrive != 1)) return BSE_EINVAL;
+  return selftest_bounded_wait(arrive, expired) == 0 ? BSE_OK : BSE_ECUDA;
+}
+
 int bse_get_stats(const bse_handle* h, bse_stats* out) {
   if (!h || !out) return BSE_EINVAL;
   *out = h->stats;

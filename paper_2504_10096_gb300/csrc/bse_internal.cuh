@@ -186,6 +186,9 @@ void launch_product_df(const Prob* dprobs, const TileJob* jobs, int njobs, int n
 void launch_split_tiles(const double2* packed, int64_t nelem, float4* split, cudaStream_t s);
 void launch_prod_reduce_d(const Prob* dprobs, int nprob, int maxnT, int mode, GenericIO io, cudaStream_t s);
 
+// bounded-wait self-test (k_adjoint_tc.cu): 0 on success, -1 on a CUDA error
+int selftest_bounded_wait(int arrive, int* expired_host);
+
 // Lanczos-Haydock spectrum (k_haydock.cu); device-resident recurrence state
 struct HdState {
   int j;        // current step

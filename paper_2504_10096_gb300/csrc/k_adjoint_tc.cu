@@ -368,9 +368,39 @@ k_adjoint_tc(const float* __restrict__ P, int64_t rows, int nk, int64_t N, const
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TMEM_COLS));
 }
 
+// Self-test of the bounded mbarrier wait every pipeline above relies on: with
+// arrive = 0 nothing ever completes the barrier, the wait gives up after
+// `spins` polls and the kernel reports it; with arrive = 1 the single expected
+// arrival comes first and the wait succeeds.  No fault, no unbounded loop.
+__global__ void k_wait_selftest(int arrive, long long spins, int* __restrict__ expired) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t b = smem_u32(&bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+  bool ok = false;
+  for (long long i = 0; i < spins && !ok; ++i) ok = mbar_test(b, 0u);
+  *expired = ok ? 0 : 1;
+}
+
 int g_tc_sms = 0;
 
 }  // namespace
+
+int selftest_bounded_wait(int arrive, int* expired_host) {
+  int* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return -1;
+  count_launch();
+  k_wait_selftest<<<1, 32>>>(arrive, 1ll << 20, d);
+  int h = -1;
+  const bool ok = cudaGetLastError() == cudaSuccess &&
+                  cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+  cudaFree(d);
+  if (!ok) return -1;
+  *expired_host = h;
+  return 0;
+}
 
 size_t adjoint_tc_panel_bytes(int64_t N, int k, int ph) {
   const int64_t rows = ((N + TCM - 1) / TCM) * TCM;

@@ -54,6 +54,9 @@ def test_strerror_and_validation_without_gpu(lib):
     w = (ctypes.c_double * 4)(1.0, 2.0, 3.0, 4.0)
     out = (ctypes.c_double * 4)()
     assert lib.bse_haydock(None, dummy, 1, 10, -1, 4, w, 0.1, out, None, None, None) == bse.BSE_EINVAL
+    e = ctypes.c_int(0)
+    assert lib.bse_selftest_bounded_wait(2, ctypes.byref(e)) == bse.BSE_EINVAL
+    assert lib.bse_selftest_bounded_wait(0, None) == bse.BSE_EINVAL
 
 
 def test_missing_library_fails_loudly(tmp_path):

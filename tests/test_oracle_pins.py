@@ -214,6 +214,38 @@ def test_folded_operator_identities(pd40):
     np.testing.assert_allclose(O.apply_mminus(A, B, O.apply_mplus(A, B, T)), T * om ** 2, atol=1e-10)
 
 
+@pytest.mark.parametrize("sign", [1, -1])
+def test_real_form_of_the_folded_halves(sign):
+    """Eq. 5 form used by the product kernels: on (Re u, Im u) the map
+    u -> A u + s B conj(u) is the real matrix [[U_re, -V_im], [U_im, V_re]] with
+    U = A + sB, V = A - sB (for s = +1 the paper's M_r up to y -> -y), and the
+    transpose use of a stored block (A = A^H, B = B^T) is [[U_re, U_im], [-V_im, V_re]]."""
+    rng = np.random.default_rng(11)
+    n = 7
+    A = rand_herm(n, rng, shift=2.0)
+    B = rand_sym(n, rng, scale=0.3)
+    U, V = A + sign * B, A - sign * B
+    R = np.block([[U.real, -V.imag], [U.imag, V.real]])
+    apply = O.apply_mplus if sign > 0 else O.apply_mminus
+    for _ in range(3):
+        u = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        w = apply(A, B, u)
+        np.testing.assert_allclose(R @ np.r_[u.real, u.imag], np.r_[w.real, w.imag], atol=1e-12)
+    # transpose use: column block of a stored tile acting on the row block's entries
+    RT = np.block([[U.real.T, U.imag.T], [-V.imag.T, V.real.T]])
+    np.testing.assert_allclose(RT, R.T, atol=0)
+    # the real matrix is symmetric (M+/M- self-adjoint for Re(x^H y)), and for s = +1 it is
+    # positive definite exactly when M of Eq. 2 is
+    np.testing.assert_allclose(R, R.T, atol=1e-12)
+    if sign > 0:
+        assert (np.linalg.eigvalsh(R).min() > 0) == O.is_positive_definite(A, B)
+        # and a B large enough to break positive definiteness breaks both the same way
+        Bbig = 4.0 * B / np.linalg.norm(B, 2) * np.linalg.eigvalsh(A).min()
+        Ub, Vb = A + Bbig, A - Bbig
+        Rb = np.block([[Ub.real, -Vb.imag], [Ub.imag, Vb.real]])
+        assert (np.linalg.eigvalsh(Rb).min() > 0) == O.is_positive_definite(A, Bbig)
+
+
 def test_apply_bse_block_form(pd40):
     """H X from the two stored blocks: Y1 = A X1 + B X2, Y2 = -conj(A conj X2 + B conj X1)."""
     A, B = pd40[0], pd40[1]

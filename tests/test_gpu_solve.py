@@ -216,3 +216,22 @@ def test_product_shape_tuner():
     assert np.array_equal(v1, v2) and torch.equal(z1, z2)
     s1.close()
     s2.close()
+
+
+def test_graphs_follow_a_change_of_subspace_size():
+    """Solves of different nev (hence ncv) on one handle: the step graphs are
+    recaptured for the new size and the results match a fresh handle's."""
+    A, B = problem(600, "c128", seed=83)
+    s = _solver(A, B)
+    v8, _, _ = s.solve(8, tol=1e-12)
+    v14, _, _ = s.solve(14, tol=1e-12)
+    v8b, _, _ = s.solve(8, tol=1e-12)
+    s.close()
+    f = _solver(A, B)
+    w14, _, _ = f.solve(14, tol=1e-12)
+    f.close()
+    om, _, _ = O.ph_lowest(A, B, 14)
+    np.testing.assert_allclose(v14, om, rtol=1e-10)
+    np.testing.assert_allclose(v8, om[:8], rtol=1e-10)
+    assert np.array_equal(v8, v8b)
+    assert np.array_equal(v14, w14)

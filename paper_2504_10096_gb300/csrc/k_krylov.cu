@@ -126,21 +126,6 @@ k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec) {
   }
 }
 
-// coef[pass][c] = sum_rb cpart[rb][c] (PH: real part only).
-__global__ void k_cgs_coef(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
-  const Prob& p = probs[blockIdx.y];
-  const KState* st = p.st;
-  if (!kphase(st, newvec)) return;
-  const int j = st->j;
-  const int nset = (j + 1) + (ph ? st->ntw : 0);
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nset) return;
-  const double2* cp = (const double2*)p.cpart;
-  double2 s = mk(0.0, 0.0);
-  for (int rb = 0; rb < p.nrb; ++rb) s = cadd(s, cp[(int64_t)rb * p.ncol + c]);
-  if (ph) s.y = 0.0;
-  ((double2*)p.coef)[(int64_t)pass * p.ncol + c] = s;
-}
 
 // w[row] -= sum_c V[row, col(c)] coef[pass][c].  grid (ceil(maxNpad/32), nprob),
 // 8 warps: lane = row of a 32-row slab, warp w takes the set entries c = w mod 8
@@ -161,8 +146,17 @@ k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
   if ((int64_t)blockIdx.x * 32 >= p.Npad) return;     // whole block (Npad is a multiple of 128)
   const int j = st->j;
   const int nset = (j + 1) + (ph ? st->ntw : 0);
-  const double2* coef = (const double2*)p.coef + (int64_t)pass * p.ncol;
-  for (int c = threadIdx.x; c < nset; c += blockDim.x) cf[c] = ccvt<ST>(coef[c]);
+  // coefficients: the row-block partial sums of the dots, added in row-block order (PH: real
+  // part only); the first row slab also stores them for k_step_finish
+  const double2* cp = (const double2*)p.cpart;
+  double2* coef = (double2*)p.coef + (int64_t)pass * p.ncol;
+  for (int c = threadIdx.x; c < nset; c += blockDim.x) {
+    double2 sc = mk(0.0, 0.0);
+    for (int rb = 0; rb < p.nrb; ++rb) sc = cadd(sc, cp[(int64_t)rb * p.ncol + c]);
+    if (ph) sc.y = 0.0;
+    cf[c] = ccvt<ST>(sc);
+    if (blockIdx.x == 0) coef[c] = sc;
+  }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const ST* V = (const ST*)p.V;
@@ -507,11 +501,10 @@ template <typename ST>
 void launch_step_cgs(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t maxNpad, int ncol,
                      int pass, cudaStream_t s) {
   // pass: 0/1 regular step passes; 2/3 the same for a fresh (replacement) vector
-  count_launch(3);
+  count_launch(2);
   const int newvec = pass >= 2 ? 1 : 0;
   const int ps = pass & 1;
   k_cgs_dot<ST><<<dim3((ncol + 1) / 2, maxnrb, nprob), 256, 0, s>>>(dprobs, ph, newvec);
-  k_cgs_coef<<<dim3((ncol + 255) / 256, nprob), 256, 0, s>>>(dprobs, ph, ps, newvec);
   k_cgs_update<ST><<<dim3((unsigned)((maxNpad + 31) / 32), nprob), 256, 0, s>>>(dprobs, ph, ps, newvec);
 }
 

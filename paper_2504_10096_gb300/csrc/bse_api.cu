@@ -181,8 +181,7 @@ int nrb_of(int64_t Npad) { return (int)((Npad + ROWBLK - 1) / ROWBLK); }
 template <typename T>
 int pack_matrix(bse_handle* h, const T* src, int64_t N, int nT, int herm, int where, T* dst) {
   if (where == BSE_DEVICE) {
-    for (int I = 0; I < nT; ++I)
-      launch_pack_row<T, T>(src + (int64_t)I * TS * N, N, nT, I, herm, dst, h->stream);
+    launch_pack_all<T, T>(src, N, nT, herm, dst, h->stream);
     CK(cudaGetLastError());
     return BSE_OK;
   }
@@ -1160,10 +1159,16 @@ int bse_create_batched(int count, const int64_t* N, const void* const* A, const 
       rc = pack_matrix<float2>(h, (const float2*)A[i], q.N, q.nT, 1, where, (float2*)q.A);
       if (!rc && h->ph) rc = pack_matrix<float2>(h, (const float2*)B[i], q.N, q.nT, 0, where, (float2*)q.B);
     } else {
-      rc = pack_matrix<double2>(h, (const double2*)A[i], q.N, q.nT, 1, where, (double2*)q.A);
-      if (!rc && h->ph) rc = pack_matrix<double2>(h, (const double2*)B[i], q.N, q.nT, 0, where, (double2*)q.B);
       // complex128 PH tiles are kept as P = A + B, Q = A - B (8 FMAs per element pair)
-      if (!rc && h->ph) launch_pq_combine((double2*)q.A, (double2*)q.B, q.ntiles * TS * TS, h->stream);
+      if (h->ph && where == BSE_DEVICE) {
+        launch_pack_pq((const double2*)A[i], (const double2*)B[i], q.N, q.nT, (double2*)q.A, (double2*)q.B,
+                       h->stream);
+        if (cudaGetLastError() != cudaSuccess) rc = BSE_ECUDA;
+      } else {
+        rc = pack_matrix<double2>(h, (const double2*)A[i], q.N, q.nT, 1, where, (double2*)q.A);
+        if (!rc && h->ph) rc = pack_matrix<double2>(h, (const double2*)B[i], q.N, q.nT, 0, where, (double2*)q.B);
+        if (!rc && h->ph) launch_pq_combine((double2*)q.A, (double2*)q.B, q.ntiles * TS * TS, h->stream);
+      }
       if (!rc && h->df) {
         const int64_t nel = q.ntiles * TS * TS;
         if (!(rc = dalloc(&q.Ahl, sizeof(float4) * (size_t)nel)))

@@ -164,6 +164,10 @@ struct ProdShape {
 
 // complex128 PH storage: tiles of A and B become P = A + B and Q = A - B (k_product.cu)
 void launch_pq_combine(double2* a, double2* b, int64_t n, cudaStream_t s);
+// packing of device-resident full matrices in one launch (k_product.cu)
+template <typename TIn, typename TSt>
+void launch_pack_all(const TIn* src, int64_t N, int nT, int herm, TSt* dst, cudaStream_t s);
+void launch_pack_pq(const double2* A, const double2* B, int64_t N, int nT, double2* P, double2* Q, cudaStream_t s);
 
 // products (k_product.cu); ST = storage complex type, R = compute real type
 template <typename ST, typename R>

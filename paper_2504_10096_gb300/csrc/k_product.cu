@@ -351,6 +351,68 @@ k_pack_row(const TIn* __restrict__ rows, int64_t N, int nT, int I, int herm, TSt
   }
 }
 
+// element (r, c) of tile (I, J >= I) from a full row-major matrix: the upper
+// triangle as stored, the lower half of a diagonal tile mirrored (conjugated for
+// a Hermitian matrix, whose diagonal's imaginary part is dropped)
+template <typename TIn, typename TSt>
+__device__ __forceinline__ TSt pack_elem(const TIn* __restrict__ src, int64_t N, int I, int J, int r, int c,
+                                         int herm) {
+  const int64_t gi = (int64_t)I * TS + r, gj = (int64_t)J * TS + c;
+  TSt v = czero<TSt>();
+  if (gi < N && gj < N) {
+    if (I != J || r < c) {
+      v = ccvt<TSt>(src[gi * N + gj]);
+    } else if (r == c) {
+      v = ccvt<TSt>(src[gi * N + gj]);
+      if (herm) v.y = 0;
+    } else {
+      v = ccvt<TSt>(src[((int64_t)I * TS + c) * N + (int64_t)I * TS + r]);
+      if (herm) v.y = -v.y;
+    }
+  }
+  return v;
+}
+
+// every tile (I, J >= I) of a device-resident matrix in one launch: grid (nT, nT)
+template <typename TIn, typename TSt>
+__global__ void __launch_bounds__(256)
+k_pack_all(const TIn* __restrict__ src, int64_t N, int nT, int herm, TSt* __restrict__ dst) {
+  const int I = blockIdx.y, J = blockIdx.x;
+  if (J < I) return;
+  const int64_t t = (int64_t)I * nT - (int64_t)I * (I - 1) / 2 + (J - I);
+  TSt* out = dst + t * (TS * TS);
+  for (int e = threadIdx.x; e < TS * TS; e += 256) out[e] = pack_elem<TIn, TSt>(src, N, I, J, e >> 7, e & (TS - 1), herm);
+}
+
+// complex128 PH from device memory: the tiles of P = A + B and Q = A - B directly
+__global__ void __launch_bounds__(256)
+k_pack_pq(const double2* __restrict__ A, const double2* __restrict__ B, int64_t N, int nT, double2* __restrict__ P,
+          double2* __restrict__ Q) {
+  const int I = blockIdx.y, J = blockIdx.x;
+  if (J < I) return;
+  const int64_t t = (int64_t)I * nT - (int64_t)I * (I - 1) / 2 + (J - I);
+  for (int e = threadIdx.x; e < TS * TS; e += 256) {
+    const double2 a = pack_elem<double2, double2>(A, N, I, J, e >> 7, e & (TS - 1), 1);
+    const double2 b = pack_elem<double2, double2>(B, N, I, J, e >> 7, e & (TS - 1), 0);
+    P[t * (TS * TS) + e] = make_double2(a.x + b.x, a.y + b.y);
+    Q[t * (TS * TS) + e] = make_double2(a.x - b.x, a.y - b.y);
+  }
+}
+
+template <typename TIn, typename TSt>
+void launch_pack_all(const TIn* src, int64_t N, int nT, int herm, TSt* dst, cudaStream_t s) {
+  count_launch();
+  k_pack_all<TIn, TSt><<<dim3(nT, nT), 256, 0, s>>>(src, N, nT, herm, dst);
+}
+
+void launch_pack_pq(const double2* A, const double2* B, int64_t N, int nT, double2* P, double2* Q, cudaStream_t s) {
+  count_launch();
+  k_pack_pq<<<dim3(nT, nT), 256, 0, s>>>(A, B, N, nT, P, Q);
+}
+
+template void launch_pack_all<double2, double2>(const double2*, int64_t, int, int, double2*, cudaStream_t);
+template void launch_pack_all<float2, float2>(const float2*, int64_t, int, int, float2*, cudaStream_t);
+
 template <typename TIn, typename TSt>
 void launch_pack_row(const TIn* rows, int64_t N, int nT, int I, int herm, TSt* dst, cudaStream_t s) {
   count_launch();

@@ -4,9 +4,10 @@
 // (and of B) exactly once per product and uses it for both block rows:
 //     y_I += A_IJ x_J + s B_IJ conj(x_J)
 //     y_J += A_IJ^H x_I + s B_IJ^T conj(x_I)        (I < J)
-// because A = A^H and B = B^T.  This is the matrix-vector product that the
-// paper identifies as the most expensive step of the iterative solver
-// (Sec. 2.2.2, last paragraph).  Each tile writes its two partial block-row
+// because A = A^H and B = B^T, applied in the real form of Eq. 5 (U = A + sB,
+// V = A - sB; 8 FMAs per stored element pair, see k_prod_tiles).  This is the
+// matrix-vector product that the paper identifies as the most expensive step
+// of the iterative solver (Sec. 2.2.2, last paragraph).  Each tile writes its two partial block-row
 // results into a scratch buffer part[I][J][:] (slot (I,J) receives the
 // contribution of column block J to row block I), and k_prod_reduce sums the
 // nT slots of every block row: no atomics, deterministic rounding order.

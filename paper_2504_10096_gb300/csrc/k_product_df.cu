@@ -1,12 +1,13 @@
 // Complex128 structured product in double-FP32 ("df64") arithmetic.
 //
 // GB300 executes 2 FP64 FMAs per SM per clock but 128 FP32 operations, so
-// the FP64 product (16 FMAs per stored element pair of A and B) is bound by
-// the FP64 pipe at about 1/5 of the HBM rate.  This kernel streams the same
-// packed tiles, pre-split at creation into float pairs a = a_hi + a_lo
-// (|a_lo| <= 2^-24 |a_hi|, exact to 2^-48 relative), and evaluates every
-// complex multiply-accumulate with error-free transformations on the FP32
-// pipes:
+// the FP64 product (8 FMAs per stored element pair in the real form of Eq. 5)
+// is bound by the FP64 pipe at about 1/2.7 of the HBM rate.  The kernels here
+// stream the same packed tiles -- split at creation into float pairs
+// a = a_hi + a_lo (|a_lo| <= 2^-24 |a_hi|, exact to 2^-48 relative) for
+// complex128 handles (k_prod_tiles_df), or the exact complex64 A and B
+// (k_prod_tiles_df2, packed f32x2) -- and evaluate every real multiply-
+// accumulate with error-free transformations on the FP32 pipes:
 //   p = fl(a_hi x_hi),  e = fma(a_hi, x_hi, -p) + a_hi x_lo + a_lo x_hi
 //   (s_hi, err) = TwoSum(s_hi, p),  s_lo += err + e
 // (Dekker's product, Knuth's TwoSum; the dropped a_lo x_lo is 2^-48 of the

@@ -91,3 +91,34 @@ def test_exact_complex64_values_give_exact_u_v():
         for s in (1.0, -1.0):
             hi, lo = two_sum(a, f32(s * b))
             assert Fraction(float(hi)) + Fraction(float(lo)) == Fraction(float(a)) + Fraction(s) * Fraction(float(b))
+
+
+def tf32_rna(v):
+    """Round a float32 to TF32 (10 explicit mantissa bits), nearest, ties away
+    from zero: the cvt.rna.tf32.f32 the adjoint's panel kernel uses."""
+    b = np.float32(v).view(np.uint32)
+    b = (b + np.uint32(0x1000)) & np.uint32(0xFFFFE000)
+    return b.view(np.float32)
+
+
+def test_three_tf32_products_reach_fp32_class_accuracy():
+    """3xTF32 (hi*hi + hi*lo + lo*hi, FP32 accumulation) for the adjoint's
+    rank-2k update: the per-product error stays at the FP32 level (2^-21),
+    where one TF32 product is at 2^-10."""
+    rng = np.random.default_rng(9)
+    a = rng.standard_normal(4096).astype(np.float32)
+    b = rng.standard_normal(4096).astype(np.float32)
+    ah = tf32_rna(a); al = (a - ah).astype(np.float32)
+    bh = tf32_rna(b); bl = (b - bh).astype(np.float32)
+    # the tensor core reads the lo parts as TF32 too: model the worst case, truncation
+    trunc = lambda v: (v.view(np.uint32) & np.uint32(0xFFFFE000)).view(np.float32)
+    alt, blt = trunc(al), trunc(bl)
+    exact = a.astype(np.float64) * b.astype(np.float64)
+    three = (ah.astype(np.float64) * bh + ah.astype(np.float64) * blt + alt.astype(np.float64) * bh)
+    one = ah.astype(np.float64) * bh
+    rel3 = np.max(np.abs(three - exact) / np.abs(exact))
+    rel1 = np.max(np.abs(one - exact) / np.abs(exact))
+    assert rel3 < 2.0 ** -20
+    assert rel1 > 2.0 ** -12
+    # the split is exact: hi + lo == a, and lo fits in TF32 up to its own rounding
+    assert np.array_equal((ah + al).astype(np.float32), a)

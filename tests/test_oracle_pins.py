@@ -256,6 +256,70 @@ def test_apply_bse_block_form(pd40):
     np.testing.assert_allclose(Y[40:], -(A @ x2.conj() + B @ x1.conj()).conj(), atol=1e-12)
 
 
+def test_metric_matrix_eq3(pd40):
+    """Eq. 3: H = Omega M with M Hermitian (Eq. 2)."""
+    A, B = pd40[0], pd40[1]
+    M = O.metric_matrix(A, B)
+    np.testing.assert_allclose(M, M.conj().T, atol=0)
+    np.testing.assert_allclose(O.omega_metric(40) @ M, O.bse_hamiltonian(A, B), atol=0)
+
+
+# ------------------------------------------------------------------ residuals and Rayleigh quotients
+def test_omega_rayleigh_quotient_n1_closed_form():
+    """N = 1, H = [[a, b], [-conj b, -a]], z = (x; y): written out by hand,
+    z^H Omega H z = a(|x|^2 + |y|^2) + 2 Re(conj(x) b y) and z^H Omega z = |x|^2 - |y|^2."""
+    a, b = 2.3, 0.6 * np.exp(0.7j)
+    x = RNG.standard_normal((1, 5)) + 1j * RNG.standard_normal((1, 5))
+    y = 0.5 * (RNG.standard_normal((1, 5)) + 1j * RNG.standard_normal((1, 5)))
+    rho = O.j_rayleigh_quotients(np.array([[a]]), np.array([[b]]), x, y)
+    want = (a * (abs(x) ** 2 + abs(y) ** 2) + 2 * np.real(x.conj() * b * y)) / (abs(x) ** 2 - abs(y) ** 2)
+    np.testing.assert_allclose(rho, want[0], rtol=1e-14)
+    # on the eigenvector (a - w) x + b y = 0 it is w = sqrt(a^2 - |b|^2) (Sec. 1)
+    w = np.sqrt(a * a - abs(b) ** 2)
+    xe = np.array([[1.0 + 0.2j]])
+    ye = -(a - w) * xe / b
+    np.testing.assert_allclose(O.j_rayleigh_quotients(np.array([[a]]), np.array([[b]]), xe, ye), [w], rtol=1e-14)
+
+
+def test_omega_rayleigh_quotient_is_second_order(pd40):
+    """z^H M z / z^H Omega z is stationary at the eigenvectors of H = Omega M:
+    an O(eps) error in z gives an O(eps^2) error in omega."""
+    A, B, om, X, Y = pd40
+    rng = np.random.default_rng(3)
+    d = rng.standard_normal((80, 5)) + 1j * rng.standard_normal((80, 5))
+    d /= np.linalg.norm(d, axis=0)
+    err = []
+    for eps in (1e-3, 1e-4):
+        Z = np.vstack([X[:, :5], Y[:, :5]]) + eps * d
+        err.append(np.max(np.abs(O.j_rayleigh_quotients(A, B, Z[:40], Z[40:]) - om[:5])))
+    assert err[0] < 1e-4 and err[1] < err[0] / 50
+
+
+def test_relative_residuals_closed_forms(pd40):
+    """Exact pairs give ~0; a shift w -> w + delta gives exactly |delta| / |w + delta|
+    (H z - (w + delta) z = -delta z); the value does not depend on the scaling of z;
+    N = 1, z = (1; 0): ||(a - w, -conj b)|| / w."""
+    A, B, om, X, Y = pd40
+    assert np.max(O.relative_residuals_ph(A, B, om, X, Y)) < 1e-12
+    delta = 1e-3 * om
+    c = 2.5 * np.exp(1.1j)
+    r = O.relative_residuals_ph(A, B, om + delta, c * X, c * Y)
+    np.testing.assert_allclose(r, np.abs(delta) / np.abs(om + delta), rtol=1e-8)
+    a, b = 2.3, 0.6 * np.exp(0.7j)
+    w = np.sqrt(a * a - abs(b) ** 2)
+    r1 = O.relative_residuals_ph(np.array([[a]]), np.array([[b]]), np.array([w]),
+                                 np.array([[1.0]]), np.array([[0.0]]))
+    np.testing.assert_allclose(r1, [np.hypot(a - w, abs(b)) / w], rtol=1e-14)
+    # TDA: diagonal A, x = e1 + e2 (not an eigenvector)
+    lam, x = 1.7, np.zeros((3, 1), complex)
+    x[0, 0] = x[1, 0] = 1.0
+    At = np.diag([1.0, 2.0, 3.0]).astype(complex)
+    rt = O.relative_residuals_tda(At, np.array([lam]), x)
+    np.testing.assert_allclose(rt, [np.hypot(1.0 - lam, 2.0 - lam) / (lam * np.sqrt(2.0))], rtol=1e-14)
+    lt, Xt = O.tda_lowest(A, 6)
+    assert np.max(O.relative_residuals_tda(A, lt, Xt)) < 1e-13
+
+
 # ------------------------------------------------------------------ gradients (FD)
 def _fd_dirs(n, rng, count):
     out = []

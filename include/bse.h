@@ -94,7 +94,9 @@ typedef enum bse_op {
 /* Solver options.  Zero-initialise and set what you need; zero fields take
    the defaults given in brackets. */
 typedef struct bse_solve_opts {
-  int ncv;            /* Krylov subspace size m [max(2 nev, nev + 32), <= N] */
+  int ncv;            /* Krylov subspace size m [max(2 nev, nev + 32)];
+                         raised to nev + 1, then capped at N (TDA, and PH
+                         with N <= 2) or N - 1 (PH, N > 2)                   */
   int maxit;          /* limit on Krylov steps [20000]                        */
   uint64_t seed;      /* start vector seed [12345]                            */
   const void* v0;     /* optional device start vector: N complex values in
@@ -177,7 +179,13 @@ int bse_create_batched(int count, const int64_t* N, const void* const* A,
  * The eigenvectors stay in the handle for bse_backward.  Method: the
  * structure-preserving thick-restart Lanczos of Sec. 2.2.1 (spectrum folding
  * for PH), eigenvector recovery and the partner relations of Eq. 7.
- * Returns BSE_ENOCONV (with *nconv_out < nev) if maxit is reached.
+ * Returns BSE_ENOCONV (with *nconv_out < nev) if maxit is reached, and
+ * BSE_EINVAL unless 1 <= nev <= N (TDA, and PH with N <= 2) or
+ * 1 <= nev <= N - 2 (PH, N > 2: the folded operator's Krylov space from one
+ * start vector has dimension N and the subspace stays one short of it).
+ * Limitation: for PH with ncv close to N (small N), pairs can be reported as
+ * converged while their FP64 residual is far above tol; the FP64 residuals
+ * are in bse_get_stats (max_residual).
  */
 int bse_solve(bse_handle* h, int nev, double tol, int which, double* eval_out,
               void* evec_out, int* nconv_out);

@@ -631,9 +631,24 @@ int solve_impl(bse_handle* h, int nev, double tol, const bse_solve_opts* opts, d
   for (auto& q : h->p) minN = std::min(minN, q.N);
   if (nev < 1 || nev > minN || !(tol > 0.0) || !eval_out) return BSE_EINVAL;
   int ncv = opts && opts->ncv > 0 ? opts->ncv : std::max(2 * nev, nev + 32);
-  if (ncv > minN) ncv = (int)minN;
-  if (ncv > MAXM) ncv = MAXM;
-  if (ncv < nev) return BSE_EINVAL;
+  // a restart keeps at least nev vectors, so a cycle adds a new Lanczos
+  // vector only when m > nev; m = nev is allowed only when it is the whole
+  // space (m = N), where one cycle is exact
+  if (ncv < nev + 1) ncv = nev + 1;
+  // Pseudo-Hermitian: every omega^2 of the folded operator is double and one
+  // chain sees one copy of each, so its Krylov space has dimension N.  A
+  // subspace that fills it ends the cycle on rounding noise, which the
+  // breakdown test need not catch at moderate N, so for N > 2 the subspace
+  // stays one short of it and nev <= N - 2.  (TDA, and N <= 2, may use the
+  // whole space.)  Accuracy still degrades when ncv is close to N: only the
+  // twins of the kept Ritz vectors are deflated, so rounding noise in the rest
+  // of the twin space can enter the basis; the FP64 residuals that the solve
+  // returns (max_residual) show it.
+  int64_t cap = std::min<int64_t>(minN, MAXM);
+  if (h->ph && minN > 2 && cap == minN) cap = minN - 1;
+  if (ncv > cap) ncv = (int)cap;
+  const bool whole = ncv == minN;     // one cycle spans the whole space: exact
+  if (ncv < nev || (ncv < nev + 1 && !whole)) return BSE_EINVAL;
   const long long maxit = opts && opts->maxit > 0 ? opts->maxit : 20000;
   const uint64_t seed = opts && opts->seed ? opts->seed : 12345ull;
   const double lock_tol = opts && opts->lock_tol > 0.0 ? opts->lock_tol : tol * 0.25;

@@ -68,3 +68,51 @@ def test_missing_library_fails_loudly(tmp_path):
             bse.load_library(str(tmp_path / "nope.so"))
     finally:
         bse._LIB = saved
+
+
+def test_more_validation_without_gpu(lib):
+    """Batched create, solve, stats and the allocation-free product reject bad
+    arguments before any CUDA call (include/bse.h states each rule)."""
+    from paper_2504_10096_gb300 import bse
+    h = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(16)
+    ns = (ctypes.c_int64 * 2)(100, 200)
+    ptrs = (ctypes.c_void_p * 2)(16, 16)
+    nulls = (ctypes.c_void_p * 2)(16, None)
+
+    def create_batched(count, n, a, b, form=1, dtype=1, where=1, out=True):
+        return lib.bse_create_batched(count, n, a, b, form, dtype, where, None,
+                                      ctypes.byref(h) if out else None)
+    assert create_batched(2, ns, ptrs, ptrs, out=False) == bse.BSE_EINVAL
+    assert create_batched(0, ns, ptrs, ptrs) == bse.BSE_EINVAL
+    assert create_batched(2, None, ptrs, ptrs) == bse.BSE_EINVAL
+    assert create_batched(2, ns, None, ptrs) == bse.BSE_EINVAL
+    assert create_batched(2, ns, ptrs, None) == bse.BSE_EINVAL          # PH without B
+    assert create_batched(2, ns, ptrs, nulls) == bse.BSE_EINVAL         # PH, one B missing
+    assert create_batched(2, ns, nulls, ptrs) == bse.BSE_EINVAL         # one A missing
+    assert create_batched(2, (ctypes.c_int64 * 2)(100, 0), ptrs, ptrs) == bse.BSE_EINVAL
+    assert create_batched(2, (ctypes.c_int64 * 2)(100, 1 << 31), ptrs, ptrs) == bse.BSE_EINVAL
+    assert create_batched(2, ns, ptrs, ptrs, form=3) == bse.BSE_EINVAL
+    assert create_batched(2, ns, ptrs, ptrs, dtype=4) == bse.BSE_EINVAL
+    assert create_batched(2, ns, ptrs, ptrs, where=2) == bse.BSE_EINVAL
+    assert h.value is None                                              # *out cleared on failure
+
+    ev = (ctypes.c_double * 4)()
+    n = ctypes.c_int(0)
+    assert lib.bse_solve(None, 4, 1e-10, 0, ev, None, ctypes.byref(n)) == bse.BSE_EINVAL
+    assert lib.bse_solve_ex(None, 4, 1e-10, 0, None, ev, None, ctypes.byref(n)) == bse.BSE_EINVAL
+    assert lib.bse_solve_batched(None, 4, 1e-10, 0, None, ev, None, None) == bse.BSE_EINVAL
+    st = bse.bse_stats()
+    assert lib.bse_get_stats(None, ctypes.byref(st)) == bse.BSE_EINVAL
+
+    def noalloc(N, A, B, dtype, op, x, y):
+        return lib.bse_apply_noalloc(N, A, B, dtype, op, x, y, None)
+    assert noalloc(0, dummy, dummy, 1, 1, dummy, dummy) == bse.BSE_EINVAL
+    assert noalloc(bse.BSE_NOALLOC_MAX_N + 1, dummy, dummy, 1, 1, dummy, dummy) == bse.BSE_EINVAL
+    assert noalloc(10, None, dummy, 1, 1, dummy, dummy) == bse.BSE_EINVAL
+    assert noalloc(10, dummy, None, 1, bse.BSE_OP_MPLUS, dummy, dummy) == bse.BSE_EINVAL
+    assert noalloc(10, dummy, None, 1, bse.BSE_OP_MMINUS, dummy, dummy) == bse.BSE_EINVAL
+    assert noalloc(10, dummy, dummy, 1, bse.BSE_OP_H, dummy, dummy) == bse.BSE_EINVAL
+    assert noalloc(10, dummy, dummy, bse.BSE_C128_DF, 1, dummy, dummy) == bse.BSE_EINVAL
+    assert noalloc(10, dummy, dummy, 1, 1, None, dummy) == bse.BSE_EINVAL
+    assert noalloc(10, dummy, dummy, 1, 1, dummy, None) == bse.BSE_EINVAL

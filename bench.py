@@ -364,7 +364,7 @@ def run_product(args):
     prob = make_problem(spec)          # host generation: no torch.linalg on the device
     stream = torch.cuda.current_stream()
     s = bse.Solver(torch.from_numpy(prob["A"]).cuda(), torch.from_numpy(prob["B"]).cuda(), stream=stream,
-                   df=args.df)
+                   df=args.df, mixed=args.mixed)
     del prob
     cdt = torch.complex128 if args.dtype == "c128" else torch.complex64
     x = torch.randn(N, dtype=cdt, device="cuda")
@@ -385,7 +385,8 @@ def run_product(args):
     byts = nmat * (N * (N + 1) / 2) * es + 3 * N * es
     flops = 8.0 * N * N          # A x (complex) or M_s x (real 2N x 2N form): 4N^2 FMAs
     peaks, kind = _peaks()
-    print(json.dumps({"mode": "product", "op": args.op, "N": N, "dtype": args.dtype, "ms": ms, "GB/s": byts / ms / 1e6,
+    print(json.dumps({"mode": "product", "op": args.op, "N": N, "dtype": args.dtype, "df": args.df,
+                      "mixed": args.mixed, "ms": ms, "GB/s": byts / ms / 1e6,
                       "TFLOP/s": flops / ms / 1e9, "hbm_frac": byts / ms / 1e6 / peaks["hbm_gbs"],
                       "hbm_peak_kind": kind}), flush=True)
     s.close()
@@ -618,6 +619,8 @@ def main():
     ap.add_argument("--df", action="store_true",
                     help="complex128 with the Lanczos products in double-FP32 arithmetic (BSE_C128_DF)")
     ap.add_argument("--fp32", action="store_true", help="mixed mode: also run plain FP32 (BSE_C64)")
+    ap.add_argument("--mixed", action="store_true",
+                    help="product mode: complex64 storage with the mixed path's double-FP32 products (BSE_C64_MIXED)")
     ap.add_argument("--ncv", type=int, default=0, help="solve mode: Krylov subspace size (0 = library default)")
     args = ap.parse_args()
     if args.warmup < 3:

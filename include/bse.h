@@ -47,8 +47,8 @@ typedef enum bse_status {
   BSE_ENOMEM = 2,     /* device or host allocation failed                       */
   BSE_ENOTPD = 3,     /* M of Eq. 2 not positive definite (negative K-norm or   */
                       /* non-positive Ritz value omega^2 met by the iteration)  */
-  BSE_ENOCONV = 4,    /* fewer than nev pairs converged within maxit steps;     */
-                      /* the converged ones are still returned                  */
+  BSE_ENOCONV = 4,    /* fewer than nev pairs passed the FP64 residual test;   */
+                      /* every computed pair is still returned                */
   BSE_ETIMEOUT = 5,   /* a device-side iteration limit expired                  */
   BSE_ECUDA = 6,      /* a CUDA runtime call failed                             */
   BSE_ESTATE = 7,     /* call out of order (e.g. backward before a solve)       */
@@ -95,8 +95,8 @@ typedef enum bse_op {
    the defaults given in brackets. */
 typedef struct bse_solve_opts {
   int ncv;            /* Krylov subspace size m [max(2 nev, nev + 32)];
-                         raised to nev + 1, then capped at N (TDA, and PH
-                         with N <= 2) or N - 1 (PH, N > 2)                   */
+                         raised to nev + 1, then capped at the smallest N
+                         of the handle (and at 1024)                          */
   int maxit;          /* limit on Krylov steps [20000]                        */
   uint64_t seed;      /* start vector seed [12345]                            */
   const void* v0;     /* optional device start vector: N complex values in
@@ -179,13 +179,16 @@ int bse_create_batched(int count, const int64_t* N, const void* const* A,
  * The eigenvectors stay in the handle for bse_backward.  Method: the
  * structure-preserving thick-restart Lanczos of Sec. 2.2.1 (spectrum folding
  * for PH), eigenvector recovery and the partner relations of Eq. 7.
- * Returns BSE_ENOCONV (with *nconv_out < nev) if maxit is reached, and
- * BSE_EINVAL unless 1 <= nev <= N (TDA, and PH with N <= 2) or
- * 1 <= nev <= N - 2 (PH, N > 2: the folded operator's Krylov space from one
- * start vector has dimension N and the subspace stays one short of it).
- * Limitation: for PH with ncv close to N (small N), pairs can be reported as
- * converged while their FP64 residual is far above tol; the FP64 residuals
- * are in bse_get_stats (max_residual).
+ *
+ * Convergence: the iteration locks a pair once its Ritz estimate is below
+ * lock_tol; after the recovery every returned pair gets an FP64 residual
+ * ||H z - rho z|| / (|rho| ||z||) with the FP64 Rayleigh quotient rho
+ * (bse_get_residuals), and only pairs whose residual is <= tol count in
+ * *nconv_out.  Returns BSE_ENOCONV if fewer than nev pairs pass that test
+ * (maxit reached, or storage/product rounding above tol, e.g. BSE_C64 with a
+ * tol near its FP32 floor); eval_out and evec_out still receive every pair
+ * that was computed (NaN eigenvalues beyond them).  BSE_EINVAL unless
+ * 1 <= nev <= N.
  */
 int bse_solve(bse_handle* h, int nev, double tol, int which, double* eval_out,
               void* evec_out, int* nconv_out);
@@ -261,9 +264,10 @@ int bse_apply(bse_handle* h, int op, int k, const void* X, void* Y);
  *   y = A x - B conj(x)    (op BSE_OP_MMINUS)
  *
  *   N       1 <= N <= BSE_NOALLOC_MAX_N (4096); larger N returns BSE_EINVAL
- *   A, B    device, full N x N row-major, complex64 (BSE_C64 / BSE_C64_MIXED)
- *           or complex128 (BSE_C128); only the upper triangles are read
- *           (A Hermitian, B symmetric); B may be NULL for BSE_OP_A
+ *   A, B    device, full N x N row-major, complex64 (dtype BSE_C64, FP32
+ *           products) or complex128 (BSE_C128, FP64 products); only the upper
+ *           triangles are read (A Hermitian, B symmetric); B may be NULL for
+ *           BSE_OP_A.  Other dtypes return BSE_EINVAL.
  *   x, y    device, N complex entries each, same dtype; must not overlap
  *   stream  cudaStream_t (NULL = legacy default stream); the call is
  *           asynchronous on it
@@ -271,9 +275,12 @@ int bse_apply(bse_handle* h, int op, int k, const void* X, void* Y);
  * Its only scratch is a fixed 2 MiB array in the library's device image
  * (every GPU that loads the library holds it until the process exits).  The
  * first call on a device looks up that array's address with the device
- * current; make that first call before any stream capture.  All calls share
- * the array: calls that overlap on the GPU (other streams or threads) race.
- * Returns BSE_EINVAL for bad arguments, BSE_ECUDA if a launch fails.
+ * current and caches it for the process; make that first call before any
+ * stream capture, and do not use this entry point across cudaDeviceReset.
+ * All calls share the array: calls that overlap on the GPU (other streams or
+ * threads) race.  Returns BSE_EINVAL for bad arguments, BSE_ECUDA if a launch
+ * fails or a CUDA error from earlier work is pending (that error is left for
+ * the caller to read).
  */
 #define BSE_NOALLOC_MAX_N 4096
 int bse_apply_noalloc(int64_t N, const void* A, const void* B, int dtype, int op,
@@ -331,6 +338,12 @@ int bse_haydock(bse_handle* h, const void* d, int where, int m, int sign,
  * a CUDA error.  The paper has no counterpart; it is a test of this build.
  */
 int bse_selftest_bounded_wait(int arrive, int* expired);
+
+/* FP64 relative residuals ||H z - rho z|| / (|rho| ||z||) of the pairs the
+   last solve returned for problem `problem` (0 for single-problem handles), in
+   output order: res_out[c] for c < n (NaN beyond the computed pairs).
+   BSE_ESTATE before the first solve, BSE_EINVAL for bad arguments. */
+int bse_get_residuals(const bse_handle* h, int problem, double* res_out, int n);
 
 /* Counters of the last solve or spectrum (single-problem handles; for
    batched handles the sums over problems). */

@@ -147,7 +147,7 @@ def shao_q(n):
 
 
 def shao_j(n):
-    """Real skew-symmetric J of Eq. 4 (not the survey's J = Omega)."""
+    """Real skew-symmetric J of Eq. 4 (not the metric Omega of Eq. 2)."""
     I = np.eye(n)
     Z = np.zeros((n, n))
     return np.block([[Z, I], [-I, Z]])

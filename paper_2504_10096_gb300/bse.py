@@ -27,7 +27,8 @@ BSE_OP_A, BSE_OP_MPLUS, BSE_OP_MMINUS, BSE_OP_H = 0, 1, 2, 3
 
 EXPORTED = ["bse_strerror", "bse_create", "bse_create_batched", "bse_solve", "bse_solve_ex",
             "bse_solve_batched", "bse_backward", "bse_apply", "bse_get_stats", "bse_destroy",
-            "bse_apply_noalloc", "bse_backward_ex", "bse_haydock", "bse_selftest_bounded_wait"]
+            "bse_apply_noalloc", "bse_backward_ex", "bse_haydock", "bse_selftest_bounded_wait",
+            "bse_get_residuals"]
 BSE_IMPL_AUTO, BSE_IMPL_CUDA_CORES, BSE_IMPL_TENSOR_CORES = 0, 1, 2
 BSE_NOALLOC_MAX_N = 4096
 
@@ -80,6 +81,7 @@ def load_library(path: str | None = None):
     lib.bse_backward.argtypes = [H, ctypes.POINTER(c_dbl), c_int, c_vp, c_vp]
     lib.bse_apply.argtypes = [H, c_int, c_int, c_vp, c_vp]
     lib.bse_get_stats.argtypes = [H, ctypes.POINTER(bse_stats)]
+    lib.bse_get_residuals.argtypes = [H, c_int, ctypes.POINTER(c_dbl), c_int]
     lib.bse_destroy.argtypes = [H]
     lib.bse_apply_noalloc.argtypes = [c_i64, c_vp, c_vp, c_int, c_int, c_vp, c_vp, c_vp]
     lib.bse_backward_ex.argtypes = [H, ctypes.POINTER(c_dbl), c_int, c_vp, c_vp, c_int]
@@ -190,6 +192,13 @@ def bse_get_stats(h) -> dict:
     s = bse_stats()
     _check(load_library().bse_get_stats(h, ctypes.byref(s)), "bse_get_stats")
     return {f: getattr(s, f) for f, _ in bse_stats._fields_}
+
+
+def bse_get_residuals(h, n, problem=0):
+    """FP64 relative residuals of the pairs the last solve returned (output order)."""
+    r = (ctypes.c_double * max(n, 1))()
+    _check(load_library().bse_get_residuals(h, int(problem), r, int(n)), "bse_get_residuals")
+    return np.array(r[:n], dtype=np.float64)
 
 
 def bse_destroy(h):
@@ -325,6 +334,10 @@ class Solver:
     def stats(self):
         return bse_get_stats(self.h)
 
+    def residuals(self):
+        """FP64 relative residual of every pair the last solve returned."""
+        return bse_get_residuals(self.h, self.nev)
+
     def close(self):
         if getattr(self, "h", None):
             bse_destroy(self.h)
@@ -340,13 +353,19 @@ class Solver:
 class BatchedSolver:
     """Many independent PH problems of uneven N solved in lock-step launches."""
 
-    def __init__(self, As, Bs, stream=None):
+    def __init__(self, As, Bs, stream=None, mixed=False):
+        """mixed=True (complex64 input only): dtype BSE_C64_MIXED for every
+        problem (complex64 storage, FP64 basis, double-FP32 products)."""
         torch = _torch()
         load_library()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.As = [a.contiguous() for a in As]
         self.Bs = [b.contiguous() for b in Bs]
         self.dtype = _dtype_code(self.As[0])
+        if mixed:
+            if self.dtype != BSE_C64:
+                raise TypeError("the mixed path needs complex64 A and B")
+            self.dtype = BSE_C64_MIXED
         self.cdtype = self.As[0].dtype
         self.Ns = [int(a.shape[0]) for a in self.As]
         self.device = self.As[0].device
@@ -364,10 +383,15 @@ class BatchedSolver:
                                             [v.data_ptr() for v in vecs] if vecs else None)
         if check:
             _check(rc, "bse_solve_batched")
+        self.nev = nev
         return vals, ([v.T for v in vecs] if vecs else None), nconv
 
     def stats(self):
         return bse_get_stats(self.h)
+
+    def residuals(self, problem):
+        """FP64 relative residuals of the pairs the last solve returned for `problem`."""
+        return bse_get_residuals(self.h, self.nev, problem)
 
     def close(self):
         if getattr(self, "h", None):
@@ -383,7 +407,12 @@ class BatchedSolver:
 
 def bse_eigenvalues(A, B, nev, tol=None, **kw):
     """Differentiable lowest eigenvalues (torch.autograd; the backward pass
-    is the library's Hellmann-Feynman adjoint kernel)."""
+    is the library's Hellmann-Feynman adjoint kernel).
+
+    The solver handle (packed A, B and the eigenvectors) lives as long as the
+    autograd graph that holds it: backward may run more than once
+    (retain_graph=True), and the handle is released when the graph is freed.
+    If neither input requires a gradient the handle is released at once."""
     torch = _torch()
 
     class _Eig(torch.autograd.Function):
@@ -391,14 +420,19 @@ def bse_eigenvalues(A, B, nev, tol=None, **kw):
         def forward(ctx, A_, B_):
             s = Solver(A_.detach(), None if B_ is None else B_.detach())
             vals, _, _ = s.solve(nev, tol=tol, **kw)
-            ctx.solver = s
+            if any(ctx.needs_input_grad):
+                ctx.solver = s
+            else:
+                s.close()
             ctx.has_b = B_ is not None
             return torch.from_numpy(vals).to(A_.device)
 
         @staticmethod
         def backward(ctx, gout):
-            dA, dB = ctx.solver.backward(gout.detach().double().cpu().numpy())
-            ctx.solver.close()
+            s = getattr(ctx, "solver", None)
+            if s is None or s.h is None:
+                raise RuntimeError("bse_eigenvalues: the solver of this graph was released")
+            dA, dB = s.backward(gout.detach().double().cpu().numpy())
             return dA, (dB if ctx.has_b else None)
 
     return _Eig.apply(A, B)

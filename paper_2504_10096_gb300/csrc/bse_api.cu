@@ -478,8 +478,9 @@ struct Driver {
     return BSE_OK;
   }
 
-  // recover eigenvectors, FP64 residuals and Rayleigh quotients of problem i
-  int finalize(int i, int nev) {
+  // recover eigenvectors, FP64 residuals and Rayleigh quotients of problem i;
+  // a pair counts as converged only if its FP64 relative residual is <= tol
+  int finalize(int i, int nev, double tol) {
     ProbHost& q = h->p[i];
     const KState& s = h->hstate[i];
     free_results(q);
@@ -536,10 +537,13 @@ struct Driver {
     std::vector<int> perm(k);
     for (int c = 0; c < k; ++c) perm[c] = c;
     std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return hr[a] < hr[b]; });
+    int good = 0;
     for (int c = 0; c < k; ++c) {
       q.eval[c] = hr[perm[c]];
       q.res[c] = hres[perm[c]];
+      if (q.res[c] <= tol) ++good;      // NaN residuals never count
     }
+    q.nconv = good;
     CK(cudaMemcpyAsync(q.perm, perm.data(), sizeof(int) * k, cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return BSE_OK;
@@ -547,13 +551,13 @@ struct Driver {
 
   int store(int i, void* out) {
     ProbHost& q = h->p[i];
-    if (!out || q.nconv == 0) return BSE_OK;
+    if (!out || q.zcols == 0) return BSE_OK;
     const int64_t ldz = h->ph ? 2 * q.Npad : q.Npad;
     const int64_t ldo = h->ph ? 2 * q.N : q.N;
     if (is_c64(h->dtype))   // caller-facing vectors in the handle's dtype
-      launch_store_vectors2<float2>(q.Z, ldz, q.Npad, q.N, h->ph, q.nconv, q.perm, (float2*)out, ldo, h->stream);
+      launch_store_vectors2<float2>(q.Z, ldz, q.Npad, q.N, h->ph, q.zcols, q.perm, (float2*)out, ldo, h->stream);
     else
-      launch_store_vectors2<double2>(q.Z, ldz, q.Npad, q.N, h->ph, q.nconv, q.perm, (double2*)out, ldo,
+      launch_store_vectors2<double2>(q.Z, ldz, q.Npad, q.N, h->ph, q.zcols, q.perm, (double2*)out, ldo,
                                      h->stream);
     CK(cudaGetLastError());
     return BSE_OK;
@@ -567,11 +571,12 @@ int alloc_solve(bse_handle* h, int ncv) {
     ProbHost& q = h->p[i];
     if (q.ncv == ncv) continue;
     free_solve_buffers(q);
-    const int ncol = 2 * ncv + 1;
+    const int ncol = 2 * ncv + 1;          // stride of the CGS partial sums and coefficients
+    const int nbas = ncv + 1;              // basis columns of V and P
     const int nrb = nrb_of(q.Npad);
     int rc;
-    if ((rc = dalloc(&q.V, es * (size_t)q.Npad * ncol))) return rc;
-    if (h->ph && (rc = dalloc(&q.P, es * (size_t)q.Npad * ncol))) return rc;
+    if ((rc = dalloc(&q.V, es * (size_t)q.Npad * nbas))) return rc;
+    if (h->ph && (rc = dalloc(&q.P, es * (size_t)q.Npad * nbas))) return rc;
     if ((rc = dalloc(&q.V2, es * (size_t)q.Npad * ncv))) return rc;
     if (h->ph && (rc = dalloc(&q.P2, es * (size_t)q.Npad * ncv))) return rc;
     if ((rc = dalloc(&q.w, es * (size_t)q.Npad))) return rc;
@@ -581,8 +586,8 @@ int alloc_solve(bse_handle* h, int ncv) {
     if ((rc = dalloc((void**)&q.coef, sizeof(double2) * 2 * (size_t)ncol))) return rc;
     if ((rc = dalloc((void**)&q.small, sizeof(double) * 6 * (size_t)(ncv + 1)))) return rc;
     if ((rc = dalloc((void**)&q.S, sizeof(double) * (size_t)ncv * ncv))) return rc;
-    CK(cudaMemsetAsync(q.V, 0, es * (size_t)q.Npad * ncol, h->stream));
-    if (h->ph) CK(cudaMemsetAsync(q.P, 0, es * (size_t)q.Npad * ncol, h->stream));
+    CK(cudaMemsetAsync(q.V, 0, es * (size_t)q.Npad * nbas, h->stream));
+    if (h->ph) CK(cudaMemsetAsync(q.P, 0, es * (size_t)q.Npad * nbas, h->stream));
     CK(cudaMemsetAsync(q.small, 0, sizeof(double) * 6 * (size_t)(ncv + 1), h->stream));
     CK(cudaMemsetAsync(q.S, 0, sizeof(double) * (size_t)ncv * ncv, h->stream));
     q.ncv = ncv;
@@ -627,27 +632,24 @@ int upload_probs(bse_handle* h) {
 template <typename ST>
 int solve_impl(bse_handle* h, int nev, double tol, const bse_solve_opts* opts, double* eval_out,
                void* const* evec_out, int* nconv_out) {
-  int64_t minN = h->p[0].N;
-  for (auto& q : h->p) minN = std::min(minN, q.N);
+  int64_t minN = h->p[0].N, maxN = h->p[0].N;
+  for (auto& q : h->p) {
+    minN = std::min(minN, q.N);
+    maxN = std::max(maxN, q.N);
+  }
   if (nev < 1 || nev > minN || !(tol > 0.0) || !eval_out) return BSE_EINVAL;
   int ncv = opts && opts->ncv > 0 ? opts->ncv : std::max(2 * nev, nev + 32);
   // a restart keeps at least nev vectors, so a cycle adds a new Lanczos
   // vector only when m > nev; m = nev is allowed only when it is the whole
-  // space (m = N), where one cycle is exact
+  // space (m = N) of every problem, where one cycle is exact.  The subspace
+  // never exceeds the smallest N: the Krylov space of one start vector has
+  // dimension <= N (on the pseudo-Hermitian path every omega^2 of the folded
+  // operator is double, one chain sees one copy, and the projection onto the
+  // twins' space keeps the other copy out).
   if (ncv < nev + 1) ncv = nev + 1;
-  // Pseudo-Hermitian: every omega^2 of the folded operator is double and one
-  // chain sees one copy of each, so its Krylov space has dimension N.  A
-  // subspace that fills it ends the cycle on rounding noise, which the
-  // breakdown test need not catch at moderate N, so for N > 2 the subspace
-  // stays one short of it and nev <= N - 2.  (TDA, and N <= 2, may use the
-  // whole space.)  Accuracy still degrades when ncv is close to N: only the
-  // twins of the kept Ritz vectors are deflated, so rounding noise in the rest
-  // of the twin space can enter the basis; the FP64 residuals that the solve
-  // returns (max_residual) show it.
-  int64_t cap = std::min<int64_t>(minN, MAXM);
-  if (h->ph && minN > 2 && cap == minN) cap = minN - 1;
+  const int64_t cap = std::min<int64_t>(minN, MAXM);
   if (ncv > cap) ncv = (int)cap;
-  const bool whole = ncv == minN;     // one cycle spans the whole space: exact
+  const bool whole = ncv == minN && minN == maxN;
   if (ncv < nev || (ncv < nev + 1 && !whole)) return BSE_EINVAL;
   const long long maxit = opts && opts->maxit > 0 ? opts->maxit : 20000;
   const uint64_t seed = opts && opts->seed ? opts->seed : 12345ull;
@@ -662,7 +664,7 @@ int solve_impl(bse_handle* h, int nev, double tol, const bse_solve_opts* opts, d
   for (int i = 0; i < h->count; ++i) {
     KState& s = h->hstate[i];
     std::memset(&s, 0, sizeof(KState));
-    s.k = 0; s.l = 0; s.j = -1; s.m = ncv; s.ntw = 0; s.nev = nev;
+    s.k = 0; s.l = 0; s.j = -1; s.m = ncv; s.nev = nev;
     s.r_pkeep = std::min(ncv - 1, nev + (ncv - nev) / 2);
     if (s.r_pkeep < nev) s.r_pkeep = nev;
     s.maxit = maxit;
@@ -693,11 +695,11 @@ int solve_impl(bse_handle* h, int nev, double tol, const bse_solve_opts* opts, d
   int64_t steps = 0, passes = 0, restarts = 0;
   int nconv_total = 0;
   for (int i = 0; i < h->count; ++i) {
-    rc = drv.finalize(i, nev);
+    rc = drv.finalize(i, nev, tol);
     if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
     const KState& s = h->hstate[i];
     ProbHost& q = h->p[i];
-    for (int c = 0; c < nev; ++c) eval_out[(size_t)i * nev + c] = c < q.nconv ? q.eval[c] : NAN;
+    for (int c = 0; c < nev; ++c) eval_out[(size_t)i * nev + c] = c < (int)q.eval.size() ? q.eval[c] : NAN;
     if (nconv_out) nconv_out[i] = q.nconv;
     for (double r : q.res) maxres = std::max(maxres, r);
     if (evec_out && evec_out[i]) {
@@ -892,7 +894,7 @@ template <typename ST>
 int backward_impl(bse_handle* h, const double* g, int where, void* dA, void* dB, int impl) {
   using R = typename std::conditional<std::is_same<ST, float2>::value, float, double>::type;
   ProbHost& q = h->p[0];
-  const int k = q.nconv;
+  const int k = q.zcols;      // every returned pair (converged or not)
   if (k == 0) return BSE_ESTATE;
   std::vector<double> gh(h->nev), gz(k, 0.0);
   if (where == BSE_DEVICE) {
@@ -902,7 +904,8 @@ int backward_impl(bse_handle* h, const double* g, int where, void* dA, void* dB,
     std::memcpy(gh.data(), g, sizeof(double) * h->nev);
   }
   std::vector<int> perm(k);
-  CK(cudaMemcpy(perm.data(), q.perm, sizeof(int) * k, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(perm.data(), q.perm, sizeof(int) * k, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
   for (int c = 0; c < k; ++c) gz[perm[c]] = gh[c];
   int rc;
   if (!h->gdev && (rc = dalloc((void**)&h->gdev, sizeof(double) * MAXM))) return rc;
@@ -1289,6 +1292,14 @@ int bse_haydock(bse_handle* h, const void* d, int where, int m, int sign, int nw
 int bse_selftest_bounded_wait(int arrive, int* expired) {
   if (!expired || (arrive != 0 && arrive != 1)) return BSE_EINVAL;
   return selftest_bounded_wait(arrive, expired) == 0 ? BSE_OK : BSE_ECUDA;
+}
+
+int bse_get_residuals(const bse_handle* h, int problem, double* res_out, int n) {
+  if (!h || !res_out || n < 0 || problem < 0 || problem >= h->count) return BSE_EINVAL;
+  if (!h->solved) return BSE_ESTATE;
+  const ProbHost& q = h->p[problem];
+  for (int c = 0; c < n; ++c) res_out[c] = c < (int)q.res.size() ? q.res[c] : NAN;
+  return BSE_OK;
 }
 
 int bse_get_stats(const bse_handle* h, bse_stats* out) {

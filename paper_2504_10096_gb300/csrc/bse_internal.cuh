@@ -7,9 +7,8 @@
 //     completion); rows and columns beyond N are zero.
 //   * vectors as Npad = nT * TS complex entries (zero padded); blocks of
 //     vectors column-major with leading dimension Npad.
-//   * the Lanczos basis V and its image P = M+ V (PH) as Npad x NCOL, with
-//     columns [0, ncv] the Krylov basis and [ncv+1, ncv+1+ncv) the "twins"
-//     i M+ y / omega of the kept Ritz vectors y.
+//   * the Lanczos basis V and its image P = M+ V (PH) as Npad x (ncv + 1),
+//     columns [0, ncv] the Krylov basis.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -74,7 +73,6 @@ struct KState {
   int l;        // kept (locked + arrow) vectors: columns [0, l)
   int j;        // index of the newest basis vector
   int m;        // ncv
-  int ntw;      // twins in use
   int nev;
   int status;   // Status
   int done;     // 1 when k >= nev (or stopped)
@@ -94,11 +92,12 @@ struct Prob {
   int64_t Npad;       // nT * TS
   int ph;             // 1 for the pseudo-Hermitian form
   int ncv;
-  int ncol;           // columns of V / P: ncv + 1 + ncv
+  int ncol;           // stride of the CGS partial sums and coefficients: 2 ncv + 1
+                      // (PH: ncv + 1 K-inner products and ncv + 1 twin coefficients)
   const void* A;      // packed tiles
   const void* B;      // packed tiles (PH) or null
-  void* V;            // Npad x ncol
-  void* P;            // Npad x ncol (PH)
+  void* V;            // Npad x (ncv + 1)
+  void* P;            // Npad x (ncv + 1) (PH)
   void* V2;           // Npad x ncv restart scratch
   void* P2;
   void* w;            // Npad work vectors

@@ -7,12 +7,22 @@
 // Re(P^H w): one pass over the stored blocks per Krylov step is spent on
 // M- p_j, the other on M+ w for the norm (the "two passes" of the step).
 //
-// Re-orthogonalisation is classical Gram-Schmidt done twice (CGS2) against
-// the whole basis, including the "twins" i M+ y / omega of the kept Ritz
-// vectors y.  The folded operator has every omega^2 twice (y and its twin),
-// and rounding noise along the twins would otherwise be amplified into
-// duplicate Ritz values; in exact arithmetic the twins are K-orthogonal to
-// the Krylov space, so removing those components changes nothing else.
+// Re-orthogonalisation is classical Gram-Schmidt done twice (CGS2).  On the
+// pseudo-Hermitian path every omega^2 of T is double: with u an eigenvector,
+// so is its "twin" i M+ u (M+(i x) = i M- x and M-(i x) = i M+ x give
+// T(i M+ u) = i M+ T u), and a Krylov space of one start vector holds one
+// direction per pair.  The
+// twins of the whole basis, i P, are K-orthogonal to the Krylov space in
+// exact arithmetic, but rounding noise along them is amplified like any
+// wanted component and would surface as duplicate Ritz values.  Each CGS
+// pass therefore also removes the K-projection of w onto span(i P): since
+// M+(i P_c) = i T v_c, <i P_c, w>_K = Im((T v_c)^H w), and the K-Gram matrix
+// of the twins, <i P_a, i P_b>_K = <v_a, T v_b>_K, is the projected matrix
+// H of the Krylov relation T V = V H + (last column); so the projection's
+// coefficients y solve H y = H s with s = Im(V^H w), i.e. y = s and
+//     w -= V Re(P^H w) + i P Im(V^H w)
+// (one extra set of Euclidean dots against V and one extra update from P,
+// no small solve).
 #include "bse_internal.cuh"
 
 namespace bse {
@@ -33,11 +43,6 @@ __device__ __forceinline__ bool kphase(const KState* st, int fresh) {
   return fresh ? kfresh(st) : kactive(st);
 }
 
-// column index of basis entry c of the orthogonalisation set [0..j] U twins
-__device__ __forceinline__ int set_col(int c, int j, int ncv) {
-  return c <= j ? c : (ncv + 1) + (c - (j + 1));
-}
-
 __device__ __forceinline__ double2 dshfl(double2 v, int m) {
   v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
   v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
@@ -45,10 +50,13 @@ __device__ __forceinline__ double2 dshfl(double2 v, int m) {
 }
 
 // ---------------------------------------------------------------- CGS2 dots
-// cpart[rb][c] = sum_{rows in block rb} conj(Q[row, col(c)]) w[row],
-// Q = P (PH) or V (TDA).  grid (ceil(maxcols/2), maxnrb, nprob), 8 warps: two
-// columns per CTA, four warps per column, each warp a quarter of the block
-// rows; the four partial sums meet in shared memory (fixed order).
+// PH: cpart[rb][c] = sum_{rows in block rb} Re(conj(P[row, c]) w[row]) for
+// c <= j (the K-inner products with the basis) and Im(conj(V[row, c']) w[row])
+// for c = j + 1 + c' (the twin coefficients s of the header), 2 (j + 1) in
+// all; TDA: the complex conj(V[row, c]) w[row], c <= j.  grid (ceil(maxcols/2),
+// maxnrb, nprob), 8 warps: two columns per CTA, four warps per column, each
+// warp a quarter of the block rows; the four partial sums meet in shared
+// memory (fixed order).
 template <typename ST>
 __global__ void __launch_bounds__(256)
 k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec) {
@@ -60,21 +68,22 @@ k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec) {
   const int rb = blockIdx.y;
   if (rb >= p.nrb) return;
   const int j = st->j;
-  const int nset = (j + 1) + (ph ? st->ntw : 0);
+  const int nset = ph ? 2 * (j + 1) : j + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int half = warp >> 2, quarter = warp & 3;
   const int c = blockIdx.x * 2 + half;
   if (blockIdx.x * 2 >= nset) return;                     // whole CTA
   double2 a = mk(0.0, 0.0);
   if (c < nset) {
-    const int col = set_col(c, j, p.ncv);
-    const ST* Q = (const ST*)(ph ? p.P : p.V) + (int64_t)col * p.Npad;
+    const bool twin = c > j;                              // warp-uniform
+    const int col = twin ? c - (j + 1) : c;
+    const ST* Q = (const ST*)(ph && !twin ? p.P : p.V) + (int64_t)col * p.Npad;
     const ST* w = (const ST*)p.w;
     const int64_t r0 = (int64_t)rb * ROWBLK + quarter * (ROWBLK / 4);
     const int64_t r1 = min((int64_t)p.Npad, r0 + ROWBLK / 4);
     // rounds of 8 rows per lane: all 16 loads of a round are issued before its arithmetic
     int64_t r = r0 + lane;
-    if (ph) {   // K-inner products are real: Re(conj(q) w) only
+    if (ph) {   // real coefficients: Re(conj(q) w), or Im(conj(v) w) = Re(conj(v) (-i w)) for twins
       R a1 = 0, a2 = 0;   // two chains (x and y products) for more ILP
       for (; r + 7 * 32 < r1; r += 8 * 32) {
         ST q[8], x[8];
@@ -83,6 +92,14 @@ k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec) {
           q[u] = __ldg(Q + r + 32 * u);
           x[u] = __ldg(w + r + 32 * u);
         }
+        if (twin) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const R t = x[u].x;
+            x[u].x = x[u].y;
+            x[u].y = -t;
+          }
+        }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           a1 = fma(q[u].x, x[u].x, a1);
@@ -90,7 +107,13 @@ k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec) {
         }
       }
       for (; r < r1; r += 32) {
-        const ST q = __ldg(Q + r), x = __ldg(w + r);
+        const ST q = __ldg(Q + r);
+        ST x = __ldg(w + r);
+        if (twin) {
+          const R t = x.x;
+          x.x = x.y;
+          x.y = -t;
+        }
         a1 = fma(q.x, x.x, a1);
         a2 = fma(q.y, x.y, a2);
       }
@@ -127,17 +150,17 @@ k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec) {
 }
 
 
-// w[row] -= sum_c V[row, col(c)] coef[pass][c].  grid (ceil(maxNpad/32), nprob),
-// 8 warps: lane = row of a 32-row slab, warp w takes the set entries c = w mod 8
-// (six or eight loads in flight each), and the eight partial sums meet in shared
-// memory.  Spreading the columns over warps keeps enough loads in flight when
-// N is only a few hundred slabs; three CTAs per SM keep N = 10^4 (316 slabs)
-// in one wave (ncu: at two per SM the last 12 CTAs ran as a second wave).
+// w[row] -= sum_{c <= j} V[row, c] coef[pass][c] (+ i sum_{c'} P[row, c'] coef[pass][j+1+c'] on the
+// PH path: the twin projection).  grid (ceil(maxNpad/32), nprob), 8 warps: lane = row of a
+// 32-row slab, warp w takes the set entries c = w mod 8 (six or eight loads in flight each),
+// and the eight partial sums meet in shared memory.  Spreading the columns over warps keeps
+// enough loads in flight when N is only a few hundred slabs; three CTAs per SM keep N = 10^4
+// (316 slabs) in one wave (ncu: at two per SM the last 12 CTAs ran as a second wave).
 template <typename ST>
 __global__ void __launch_bounds__(256, 3)
 k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
   using R = typename RealOf<ST>::T;
-  __shared__ ST cf[2 * MAXM + 1];
+  __shared__ ST cf[2 * MAXM + 2];
   __shared__ ST red[8][32];
   const Prob& p = probs[blockIdx.y];
   const KState* st = p.st;
@@ -145,7 +168,8 @@ k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
   const int64_t row = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
   if ((int64_t)blockIdx.x * 32 >= p.Npad) return;     // whole block (Npad is a multiple of 128)
   const int j = st->j;
-  const int nset = (j + 1) + (ph ? st->ntw : 0);
+  const int nj = j + 1;                     // basis columns [0, j]
+  const int nset = ph ? 2 * nj : nj;
   // coefficients: the row-block partial sums of the dots, added in row-block order (PH: real
   // part only); the first row slab also stores them for k_step_finish
   const double2* cp = (const double2*)p.cpart;
@@ -159,24 +183,30 @@ k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const ST* V = (const ST*)p.V;
-  const int nj = j + 1;                     // basis columns [0, j], then the twins
-  const ST* vb = V + row;
-  const ST* tw = V + (int64_t)(p.ncv + 1) * p.Npad + row;
+  const ST* vb = (const ST*)p.V + row;
+  const ST* pb = ph ? (const ST*)p.P + row : nullptr;
   constexpr int U = sizeof(ST) == 16 ? 6 : 8;   // loads in flight per thread (registers for 3 CTAs/SM)
   const int64_t ld = p.Npad;
-  auto colptr = [&](int cc) { return cc < nj ? vb + (int64_t)cc * ld : tw + (int64_t)(cc - nj) * ld; };
+  // entry cc of the set: V[:, cc] for cc < nj, else the twin i P[:, cc - nj] (as (-p.y, p.x))
+  auto colval = [&](int cc) -> ST {
+    if (cc < nj) return __ldg(vb + (int64_t)cc * ld);
+    const ST q = __ldg(pb + (int64_t)(cc - nj) * ld);
+    ST t;
+    t.x = -q.y;
+    t.y = q.x;
+    return t;
+  };
   ST part = czero<ST>();
   int c = warp;
   // all U loads of a round are issued before any of their arithmetic
-  if (ph) {                                 // real coefficients (K-inner products)
+  if (ph) {                                 // real coefficients (K-inner products, twin projections)
     R ax[U], ay[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) ax[u] = ay[u] = (R)0;
     for (; c + 8 * (U - 1) < nset; c += 8 * U) {
       ST v[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) v[u] = __ldg(colptr(c + 8 * u));
+      for (int u = 0; u < U; ++u) v[u] = colval(c + 8 * u);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const R f = cf[c + 8 * u].x;
@@ -185,7 +215,7 @@ k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
       }
     }
     for (; c < nset; c += 8) {
-      const ST v = __ldg(colptr(c));
+      const ST v = colval(c);
       const R f = cf[c].x;
       ax[0] = fma(v.x, f, ax[0]);
       ay[0] = fma(v.y, f, ay[0]);
@@ -202,11 +232,11 @@ k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
     for (; c + 8 * (U - 1) < nset; c += 8 * U) {
       ST v[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) v[u] = __ldg(colptr(c + 8 * u));
+      for (int u = 0; u < U; ++u) v[u] = __ldg(vb + (int64_t)(c + 8 * u) * ld);
 #pragma unroll
       for (int u = 0; u < U; ++u) cfma(acc[u], v[u], cf[c + 8 * u]);
     }
-    for (; c < nset; c += 8) cfma(acc[0], __ldg(colptr(c)), cf[c]);
+    for (; c < nset; c += 8) cfma(acc[0], __ldg(vb + (int64_t)c * ld), cf[c]);
 #pragma unroll
     for (int u = 0; u < U; ++u) part = cadd(part, acc[u]);
   }
@@ -442,43 +472,6 @@ __global__ void k_restart_copy(const Prob* __restrict__ probs, int ph) {
   }
 }
 
-// Twins of the kept vectors y_i (i < l = k0 + nkeep):
-//   t_i = i P[:, i] / w_i,  M+ t_i = i (theta_i y_i + b_i v_l) / w_i,  w_i = sqrt(theta_i)
-// (M+ t = i M- M+ y / w and M- M+ y = theta y + b v_l by the Krylov relation).
-template <typename ST>
-__global__ void k_twins(const Prob* __restrict__ probs) {
-  using R = typename RealOf<ST>::T;
-  const Prob& p = probs[blockIdx.y];
-  const KState* st = p.st;
-  if (st->status != ST_OK || !st->r_go) return;   // decided in this restart only
-  const int l = st->r_k0 + st->r_nkeep;
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= p.Npad) return;
-  const ST* V = (const ST*)p.V;
-  ST* Vw = (ST*)p.V;
-  ST* Pw = (ST*)p.P;
-  const ST vl = V[(int64_t)l * p.Npad + row];
-  const int tw0 = p.ncv + 1;
-  for (int i = 0; i < l; ++i) {
-    const double th = p.theta[i];
-    if (!(th > 0.0)) continue;
-    const double om = sqrt(th);
-    const R inv = (R)(1.0 / om);
-    const ST pi = ((const ST*)p.P)[(int64_t)i * p.Npad + row];
-    const ST yi = V[(int64_t)i * p.Npad + row];
-    ST t;   // i * pi / om
-    t.x = -pi.y * inv; t.y = pi.x * inv;
-    Vw[(int64_t)(tw0 + i) * p.Npad + row] = t;
-    const R th_r = (R)th, b = (R)p.barrow[i];
-    ST q;   // theta y + b v_l
-    q.x = th_r * yi.x + b * vl.x;
-    q.y = th_r * yi.y + b * vl.y;
-    ST pt;
-    pt.x = -q.y * inv; pt.y = q.x * inv;
-    Pw[(int64_t)(tw0 + i) * p.Npad + row] = pt;
-  }
-}
-
 __global__ void k_restart_commit(const Prob* __restrict__ probs, int nprob, int ph) {
   const int ip = blockIdx.x * blockDim.x + threadIdx.x;
   if (ip >= nprob) return;
@@ -489,7 +482,6 @@ __global__ void k_restart_commit(const Prob* __restrict__ probs, int nprob, int 
   st->k = k0 + st->r_nl;
   st->l = k0 + st->r_nkeep;
   st->j = st->l;
-  st->ntw = ph ? st->l : 0;
   st->restarts += 1;
   st->r_go = 0;
   if (st->k >= st->nev) st->done = 1;
@@ -529,13 +521,12 @@ void launch_start_vector(const Prob* dprobs, int nprob, int64_t maxNpad, uint64_
 
 template <typename ST>
 void launch_restart(const Prob* dprobs, int nprob, int ph, int64_t maxNpad, int ncv, cudaStream_t s) {
-  count_launch(ph ? 5 : 3);
+  count_launch(ph ? 4 : 3);
   const unsigned gx = (unsigned)((maxNpad + 63) / 64);
   k_restart_gemm<ST><<<dim3(gx, (ncv + 15) / 16, nprob), 256, 0, s>>>(dprobs, 0);
   if (ph) k_restart_gemm<ST><<<dim3(gx, (ncv + 15) / 16, nprob), 256, 0, s>>>(dprobs, 1);
   const unsigned gr = (unsigned)((maxNpad + 255) / 256);
   k_restart_copy<ST><<<dim3(gr, nprob), 256, 0, s>>>(dprobs, ph);
-  if (ph) k_twins<ST><<<dim3(gr, nprob), 256, 0, s>>>(dprobs);
   k_restart_commit<<<(nprob + 127) / 128, 128, 0, s>>>(dprobs, nprob, ph);
 }
 

@@ -14,7 +14,9 @@
 // device, with the device current) and passed to the kernels.  All calls share
 // the array, so calls that overlap on the GPU (different streams, or threads)
 // race on it.  Every partial-sum slot a call reads is written earlier in the
-// same call, so nothing has to be cleared between calls.
+// same call, so nothing has to be cleared between calls.  The looked-up
+// address is cached per device for the life of the process, so this entry
+// point does not support cudaDeviceReset (the cached address would be stale).
 #include <mutex>
 
 #include "../../include/bse.h"
@@ -174,12 +176,14 @@ int na_run(int64_t N, const void* A, const void* B, int op, const void* x, void*
   const int ntiles = nT * (nT + 1) / 2;
   const R sB = op == BSE_OP_MPLUS ? (R)1 : (op == BSE_OP_MMINUS ? (R)-1 : (R)0);
   CT* part = (CT*)scratch;
+  // an error pending from the caller's own earlier work is left for the caller to read
+  if (cudaPeekAtLastError() != cudaSuccess) return BSE_ECUDA;
   if (op == BSE_OP_A)
     k_na_tiles<R, false><<<ntiles, 256, 0, s>>>(N, nT, (const CT*)A, nullptr, sB, (const CT*)x, part);
   else
     k_na_tiles<R, true><<<ntiles, 256, 0, s>>>(N, nT, (const CT*)A, (const CT*)B, sB, (const CT*)x, part);
   k_na_reduce<R><<<nT, TS, 0, s>>>(N, nT, part, (CT*)y);
-  return cudaGetLastError() == cudaSuccess ? BSE_OK : BSE_ECUDA;
+  return cudaGetLastError() == cudaSuccess ? BSE_OK : BSE_ECUDA;   // no error was pending: it is ours
 }
 
 }  // namespace
@@ -190,7 +194,7 @@ extern "C" int bse_apply_noalloc(int64_t N, const void* A, const void* B, int dt
   if (N < 1 || N > BSE_NOALLOC_MAX_N || !A || !x || !y) return BSE_EINVAL;
   if (op != BSE_OP_A && op != BSE_OP_MPLUS && op != BSE_OP_MMINUS) return BSE_EINVAL;
   if (op != BSE_OP_A && !B) return BSE_EINVAL;
-  if (dtype != BSE_C64 && dtype != BSE_C128 && dtype != BSE_C64_MIXED) return BSE_EINVAL;
+  if (dtype != BSE_C64 && dtype != BSE_C128) return BSE_EINVAL;
   void* scratch = nullptr;
   const int rc = bse::scratch_address(&scratch);
   if (rc != BSE_OK) return rc;

@@ -36,6 +36,8 @@ __all__ = [
     "batched_specs",
     "loss_draws",
     "random_start",
+    "reduced_spec",
+    "gradient_probe_entries",
 ]
 
 
@@ -257,6 +259,37 @@ def loss_draws(nev: int, seed: int = 3):
     w = rng.uniform(0.0, 1.0, nev)
     noise = rng.normal(0.0, 0.01, nev)
     return w, noise
+
+
+def reduced_spec(index: int, n: int) -> BSEProblemSpec:
+    """The recipe of workload `index` (seed, N_G, energy window, kernel norms,
+    storage type, nev) at a smaller order n, for the dense oracle to reach."""
+    return dataclasses.replace(CONFIGS[index], n=int(n))
+
+
+# the seven perturbation directions of a Hermitian A / symmetric B entry
+PROBE_KINDS = ("A_re", "A_im", "A_diag", "B_re", "B_im", "B_diag_re", "B_diag_im")
+
+
+def gradient_probe_entries(n: int, focus: int, counts=(10, 10, 8, 10, 10, 8, 8), seed: int = 31):
+    """Seeded entries (kind, i, j) at which a gradient is probed: off-diagonal
+    entries (i < j) for the *_re / *_im kinds, diagonal ones (i == j) for the
+    *_diag kinds; `counts` per kind in the order of PROBE_KINDS (64 in all).
+    Three in four indices are drawn from [0, focus) -- with the transition
+    energies sorted ascending, the lowest eigenvectors live mostly there, so
+    those entries carry gradients well above rounding -- the rest from [0, n)."""
+    rng = np.random.default_rng([seed, n])
+    out = []
+    for kind, c in zip(PROBE_KINDS, counts):
+        for t in range(c):
+            hi = n if t % 4 == 3 else min(n, focus)
+            if "diag" in kind:
+                i = int(rng.integers(0, hi))
+                out.append((kind, i, i))
+            else:
+                i, j = sorted(int(v) for v in rng.choice(hi, 2, replace=False))
+                out.append((kind, i, j))
+    return out
 
 
 def random_start(n: int, seed: int = 12345) -> np.ndarray:

@@ -25,3 +25,31 @@ def omega_metric_apply(Z):
     out = Z.copy()
     out[n:] *= -1
     return out
+
+
+# unit roundoff of the storage precision of the product tests
+UNIT = {"c128": 2.0 ** -53, "c64": 2.0 ** -24}
+
+
+def product_bound(A, B, X, op):
+    """Element-wise magnitude |M| |X| that bounds the rounding of Y = M X
+    (M = A, M+/M- with both blocks, or H of Eq. 1 for op "h"), in FP64."""
+    aA = np.abs(np.asarray(A, dtype=np.complex128))
+    aX = np.abs(np.asarray(X, dtype=np.complex128))
+    if op == "a":
+        return aA @ aX
+    aB = np.abs(np.asarray(B, dtype=np.complex128))
+    if op in ("mplus", "mminus"):
+        return aA @ aX + aB @ aX
+    n = aA.shape[0]
+    x1, x2 = aX[:n], aX[n:]
+    return np.vstack([aA @ x1 + aB @ x2, aB @ x1 + aA @ x2])
+
+
+def assert_elementwise(Y, Yref, bound, u, c, what=""):
+    """|Y - Yref| <= c u bound element by element (bound from product_bound)."""
+    err = np.abs(np.asarray(Y, dtype=np.complex128) - np.asarray(Yref, dtype=np.complex128))
+    lim = c * u * np.asarray(bound) + 1e-300
+    worst = float(np.max(err / lim))
+    assert worst <= 1.0, f"{what}: element error reaches {worst:.3g} x the bound {c} u |M||x|"
+    return worst

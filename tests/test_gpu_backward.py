@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from tests.gpu_common import problem, rel
+from tests.gpu_common import problem, rand_block, rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -44,7 +44,7 @@ def test_backward_c64_error_stated():
     from paper_2504_10096_gb300 import bse
     n, nev = 300, 6
     A, B = problem(n, "c64", seed=35)
-    s = bse.Solver(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda())
+    s = bse.Solver(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), mixed=True)
     s.solve(nev, tol=1e-6)
     g = np.ones(nev)
     dA, dB = s.backward(g)
@@ -61,7 +61,7 @@ def test_backward_tensor_cores_match_cuda_cores(form, n, nev):
     same eigenvectors: ragged tiles, several K chunks, more tiles than SMs."""
     from paper_2504_10096_gb300 import bse
     A, B = problem(n, "c64", form=form, seed=41 + n)
-    s = bse.Solver(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda() if form == "ph" else None)
+    s = bse.Solver(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda() if form == "ph" else None, mixed=True)
     s.solve(nev, tol=1e-6)
     g = np.random.default_rng(5).uniform(-1.0, 1.0, nev)
     dA1, dB1 = s.backward(g, impl=bse.BSE_IMPL_CUDA_CORES)
@@ -73,6 +73,45 @@ def test_backward_tensor_cores_match_cuda_cores(form, n, nev):
         b1, b2 = dB1.cpu().numpy(), dB2.cpu().numpy()
         assert rel(b2, b1) < 2e-5
         assert np.array_equal(b2, b2.T)
+    s.close()
+
+
+@pytest.mark.parametrize("form,n,nev", [("ph", 300, 6), ("ph", 1000, 40), ("tda", 333, 5)])
+def test_tensor_core_adjoint_elementwise_on_own_vectors(form, n, nev):
+    """k_adjoint_tc against oracle.hf_gradient_ph / hf_gradient_tda evaluated on
+    the GPU's own returned eigenvectors, entry by entry: this isolates the
+    tcgen05 kernel (3xTF32 products, FP32 accumulation in tensor memory,
+    complex64 output) from the eigenvector error of the solve.  Bound per
+    entry: (8 2^-21 + 3 K 2^-23) (sum_k |g_k| (|X_ik||X_jk| + |Y_ik||Y_jk|)) for
+    G_A, the same with |X_ik||Y_jk| + |Y_ik||X_jk| for G_B: three TF32 hi/lo
+    products per term (the dropped lo x lo and the lo parts' own rounding, a few
+    2^-22), K = 2 nev (PH) or nev (TDA) rank-one terms, each three MMAs,
+    accumulated in FP32."""
+    from paper_2504_10096_gb300 import bse
+    A, B = problem(n, "c64", form=form, seed=51 + n)
+    s = bse.Solver(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda() if form == "ph" else None, mixed=True)
+    _, vecs, _ = s.solve(nev, tol=1e-8)
+    g = np.random.default_rng(7).uniform(-1.0, 1.0, nev)
+    dA, dB = s.backward(g, impl=bse.BSE_IMPL_TENSOR_CORES)
+    Z = vecs.cpu().numpy().astype(np.complex128)
+    ag = np.abs(g)
+    if form == "ph":
+        X, Y = Z[:n], Z[n:]
+        GA, GB = O.hf_gradient_ph(X, Y, g)
+        aX, aY = np.abs(X), np.abs(Y)
+        bA = (aX * ag) @ aX.T + (aY * ag) @ aY.T
+        bB = (aX * ag) @ aY.T + ((aX * ag) @ aY.T).T
+        pairs = ((dA, GA, bA), (dB, GB, bB))
+    else:
+        GA = O.hf_gradient_tda(Z, g)
+        aX = np.abs(Z)
+        pairs = ((dA, GA, (aX * ag) @ aX.T),)
+    K = 2 * nev if form == "ph" else nev
+    c = 8 * 2.0 ** -21 + 3 * K * 2.0 ** -23
+    for got, ref, bnd in pairs:
+        err = np.abs(got.cpu().numpy().astype(np.complex128) - ref)
+        worst = float(np.max(err / (c * bnd + 1e-30)))
+        assert worst <= 1.0, worst
     s.close()
 
 

@@ -1,12 +1,15 @@
 """Edge cases of the iterative solver at the smallest sizes, against the dense oracle.
 
 * N = 1 (closed forms: lambda = a for TDA, omega = sqrt(a^2 - |b|^2) for PH, Sec. 1);
-* the subspace is the whole space (TDA, and N <= 2; ncv capped at N): one
-  cycle reaches an invariant subspace and must lock everything;
-* pseudo-Hermitian with N > 2: the subspace stays one short of the folded
-  operator's N-dimensional Krylov space, so nev > N - 2 is rejected;
+* the subspace is the whole space (ncv capped at N, both forms): one cycle
+  reaches an invariant subspace and must lock everything;
+* pseudo-Hermitian with the subspace close to or equal to N (the folded
+  operator's N-dimensional Krylov space): the projection onto the twins' space
+  keeps the second copy of every omega^2 out, so the pairs reach tol;
 * a caller-given ncv equal to nev (raised to nev + 1 so that every cycle adds a
-  new Lanczos vector)."""
+  new Lanczos vector);
+* a batch whose smallest problem caps ncv at nev while a larger one needs
+  more: rejected (no cycle could add a vector to the larger problem)."""
 import numpy as np
 import pytest
 
@@ -53,24 +56,41 @@ def _check_pairs(form, A, B, n, nev, vals, vecs, nconv):
     assert res.max() < 1e-11
 
 
-@pytest.mark.parametrize("form,n,nev", [("tda", 40, 40), ("tda", 40, 10), ("tda", 2, 2), ("ph", 2, 2)])
+@pytest.mark.parametrize("form,n,nev", [("tda", 40, 40), ("tda", 40, 10), ("tda", 2, 2), ("ph", 2, 2),
+                                        ("ph", 40, 40), ("ph", 40, 39), ("ph", 40, 10)])
 def test_subspace_is_the_whole_space(form, n, nev):
     """ncv is capped at N: the first cycle reaches an invariant subspace."""
     A, B = problem(n, "c128", form=form, seed=100 + n + nev)
     s = _solver(A, B if form == "ph" else None)
     vals, vecs, nconv = s.solve(nev, tol=1e-12)
     _check_pairs(form, A, B, n, nev, vals, vecs, nconv)
+    assert s.residuals().max() <= 1e-12
     s.close()
 
 
-@pytest.mark.parametrize("nev", [39, 40])
-def test_ph_nev_above_n_minus_2_is_rejected(nev):
-    from paper_2504_10096_gb300 import bse
-    A, B = problem(40, "c128", form="ph", seed=140)
+@pytest.mark.parametrize("nev,ncv", [(10, 39), (38, 39), (10, 40), (39, 40)])
+def test_ph_subspace_close_to_n(nev, ncv):
+    """Pseudo-Hermitian N = 40 with ncv = N - 1 or N: every counted pair has an
+    FP64 residual <= tol and the eigenvalues match the dense oracle to 1e-11."""
+    A, B = problem(40, "c128", form="ph", seed=140 + nev)
     s = _solver(A, B)
-    rc, _, _ = bse.bse_solve(s.h, nev, 1e-12)
-    assert rc == bse.BSE_EINVAL
+    vals, vecs, nconv = s.solve(nev, tol=1e-12, ncv=ncv)
+    _check_pairs("ph", A, B, 40, nev, vals, vecs, nconv)
+    assert s.residuals().max() <= 1e-12
     s.close()
+
+
+def test_batched_ncv_capped_at_nev_is_rejected():
+    """N = {5, 200}, nev = 5: the smallest problem caps ncv at 5 = nev, which
+    is the whole space of that problem but would let the larger one restart
+    without adding a vector; the solve is refused with BSE_EINVAL."""
+    from paper_2504_10096_gb300 import bse
+    probs = [problem(n, "c128", form="ph", seed=150 + n) for n in (5, 200)]
+    bs = bse.BatchedSolver([torch.from_numpy(a).cuda() for a, _ in probs],
+                           [torch.from_numpy(b).cuda() for _, b in probs])
+    rc, _, _ = bse.bse_solve_batched(bs.h, 2, 5, 1e-12)
+    assert rc == bse.BSE_EINVAL
+    bs.close()
 
 
 @pytest.mark.parametrize("form", ["tda", "ph"])

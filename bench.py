@@ -366,16 +366,28 @@ def run_product(args):
     s = bse.Solver(torch.from_numpy(prob["A"]).cuda(), torch.from_numpy(prob["B"]).cuda(), stream=stream,
                    df=args.df, mixed=args.mixed)
     del prob
-    cdt = torch.complex128 if args.dtype == "c128" else torch.complex64
+    cdt = torch.complex128 if (args.dtype == "c128" or args.mixed) else torch.complex64
     x = torch.randn(N, dtype=cdt, device="cuda")
     op = bse.BSE_OP_A if args.op == "a" else bse.BSE_OP_MPLUS
+    if args.mixed:
+        # the mixed path's own product (complex128 vectors): exact double-FP32 tiles and,
+        # with --tau >= 0, coarse tiles on the fixed-point grid (bse_apply_mixed)
+        y = torch.empty_like(x)
+
+        def apply():
+            rc = bse.bse_apply_mixed(s.h, op, args.tau, x.data_ptr(), y.data_ptr())
+            if rc != bse.BSE_OK:
+                raise bse.BSEError(rc, "bse_apply_mixed")
+    else:
+        def apply():
+            s.apply(op, x)
     for _ in range(args.warmup):
-        s.apply(op, x)
+        apply()
     times = []
     for _ in range(max(args.steps, 10)):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        s.apply(op, x)
+        apply()
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -385,8 +397,11 @@ def run_product(args):
     byts = nmat * (N * (N + 1) / 2) * es + 3 * N * es
     flops = 8.0 * N * N          # A x (complex) or M_s x (real 2N x 2N form): 4N^2 FMAs
     peaks, kind = _peaks()
+    st = s.stats()
     print(json.dumps({"mode": "product", "op": args.op, "N": N, "dtype": args.dtype, "df": args.df,
-                      "mixed": args.mixed, "ms": ms, "GB/s": byts / ms / 1e6,
+                      "mixed": args.mixed, "tau": args.tau if args.mixed else None,
+                      "tiles_fine": st["tiles_fine"] if args.mixed else None,
+                      "tiles_coarse": st["tiles_coarse"] if args.mixed else None, "ms": ms, "GB/s": byts / ms / 1e6,
                       "TFLOP/s": flops / ms / 1e9, "hbm_frac": byts / ms / 1e6 / peaks["hbm_gbs"],
                       "hbm_peak_kind": kind}), flush=True)
     s.close()
@@ -620,7 +635,9 @@ def main():
                     help="complex128 with the Lanczos products in double-FP32 arithmetic (BSE_C128_DF)")
     ap.add_argument("--fp32", action="store_true", help="mixed mode: also run plain FP32 (BSE_C64)")
     ap.add_argument("--mixed", action="store_true",
-                    help="product mode: complex64 storage with the mixed path's double-FP32 products (BSE_C64_MIXED)")
+                    help="product mode: complex64 storage with the mixed path's products (BSE_C64_MIXED)")
+    ap.add_argument("--tau", type=float, default=0.0,
+                    help="product mode with --mixed: tile threshold (0: the tol-1e-6 default, <0: every tile exact)")
     ap.add_argument("--ncv", type=int, default=0, help="solve mode: Krylov subspace size (0 = library default)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -109,6 +109,18 @@ typedef struct bse_solve_opts {
                          as CUDA graphs of 1, 2, 4, ... steps, captured once
                          per handle and subspace size; nonzero: every kernel
                          is launched on the stream one by one [0]             */
+  double tile_tau;    /* BSE_C64_MIXED with B only: a packed tile whose bound
+                         on |A + B|, |A - B| (per component) is at most
+                         tile_tau times the largest tile bound of its problem
+                         is "coarse": its U = A + s B, V = A - s B are rounded
+                         to FP32 (a fixed perturbation of <= 2^-24 |U| per
+                         entry) and its products accumulated on a fixed-point
+                         grid (about 2^-35 of the tile's scale); the others
+                         get exact double-FP32 products.  Negative: every
+                         tile exact.  [min(2^-7, tol 2^24 / (16 sqrt(N)))].
+                         If a solve with coarse tiles leaves a pair above tol
+                         on the FP64 residual check before maxit, it is
+                         repeated with every tile exact (retried_exact).      */
 } bse_solve_opts;
 
 /* Per-solve counters, filled by bse_get_stats after a solve. */
@@ -127,6 +139,10 @@ typedef struct bse_stats {
                             contiguous run                                    */
   int tuned;             /* 1 once the shape was chosen by timing (bse_solve
                             times the candidates on its own first products)   */
+  int64_t tiles_fine;    /* packed tiles per product on the exact path        */
+  int64_t tiles_coarse;  /* mixed path: tiles with rounded U, V (tile_tau)    */
+  int retried_exact;     /* 1 if the last solve was repeated with every tile
+                            exact after its FP64 residual check failed        */
 } bse_stats;
 
 /* Human-readable message for a status code (static storage). */
@@ -249,6 +265,20 @@ int bse_backward_ex(bse_handle* h, const double* dL_dlambda, int where, void* dA
  * rows (A = A^H, B = B^T).  Only for single-problem handles.
  */
 int bse_apply(bse_handle* h, int op, int k, const void* X, void* Y);
+
+/*
+ * bse_apply_mixed -- the mixed path's Lanczos product on one vector:
+ *   y = A x + B conj(x)   (op BSE_OP_MPLUS)
+ *   y = A x - B conj(x)   (op BSE_OP_MMINUS)
+ * for a BSE_C64_MIXED pseudo-Hermitian handle, with x and y device arrays of
+ * N complex128 values (the precision of that path's Krylov basis).  Tiles are
+ * split into exact and coarse ones as in a solve (bse_solve_opts.tile_tau):
+ * tile_tau > 0 sets the threshold, tile_tau < 0 makes every tile exact, 0
+ * takes the default of a solve at tol = 1e-6.  bse_get_stats then reports
+ * tiles_fine / tiles_coarse.  Same real form of Eq. 5 as the solver's
+ * product; BSE_EINVAL for other handles or ops.
+ */
+int bse_apply_mixed(bse_handle* h, int op, double tile_tau, const void* X, void* Y);
 
 /*
  * bse_apply_noalloc -- one structured product that allocates no device memory.

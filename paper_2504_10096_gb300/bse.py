@@ -28,7 +28,7 @@ BSE_OP_A, BSE_OP_MPLUS, BSE_OP_MMINUS, BSE_OP_H = 0, 1, 2, 3
 EXPORTED = ["bse_strerror", "bse_create", "bse_create_batched", "bse_solve", "bse_solve_ex",
             "bse_solve_batched", "bse_backward", "bse_apply", "bse_get_stats", "bse_destroy",
             "bse_apply_noalloc", "bse_backward_ex", "bse_haydock", "bse_selftest_bounded_wait",
-            "bse_get_residuals"]
+            "bse_get_residuals", "bse_apply_mixed"]
 BSE_IMPL_AUTO, BSE_IMPL_CUDA_CORES, BSE_IMPL_TENSOR_CORES = 0, 1, 2
 BSE_NOALLOC_MAX_N = 4096
 
@@ -36,7 +36,7 @@ BSE_NOALLOC_MAX_N = 4096
 class bse_solve_opts(ctypes.Structure):
     _fields_ = [("ncv", ctypes.c_int), ("maxit", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("v0", ctypes.c_void_p), ("lock_tol", ctypes.c_double),
-                ("stream_launches", ctypes.c_int)]
+                ("stream_launches", ctypes.c_int), ("tile_tau", ctypes.c_double)]
 
 
 class bse_stats(ctypes.Structure):
@@ -44,7 +44,9 @@ class bse_stats(ctypes.Structure):
                 ("nconv", ctypes.c_int), ("max_residual", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_product", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("shape_ctas_per_sm", ctypes.c_int),
-                ("shape_strided", ctypes.c_int), ("tuned", ctypes.c_int)]
+                ("shape_strided", ctypes.c_int), ("tuned", ctypes.c_int),
+                ("tiles_fine", ctypes.c_int64), ("tiles_coarse", ctypes.c_int64),
+                ("retried_exact", ctypes.c_int)]
 
 
 class BSEError(RuntimeError):
@@ -82,6 +84,7 @@ def load_library(path: str | None = None):
     lib.bse_apply.argtypes = [H, c_int, c_int, c_vp, c_vp]
     lib.bse_get_stats.argtypes = [H, ctypes.POINTER(bse_stats)]
     lib.bse_get_residuals.argtypes = [H, c_int, ctypes.POINTER(c_dbl), c_int]
+    lib.bse_apply_mixed.argtypes = [H, c_int, c_dbl, c_vp, c_vp]
     lib.bse_destroy.argtypes = [H]
     lib.bse_apply_noalloc.argtypes = [c_i64, c_vp, c_vp, c_int, c_int, c_vp, c_vp, c_vp]
     lib.bse_backward_ex.argtypes = [H, ctypes.POINTER(c_dbl), c_int, c_vp, c_vp, c_int]
@@ -183,6 +186,11 @@ def bse_apply(h, op, k, X_ptr, Y_ptr):
     return load_library().bse_apply(h, op, k, X_ptr, Y_ptr)
 
 
+def bse_apply_mixed(h, op, tile_tau, x_ptr, y_ptr):
+    """The mixed path's product on one complex128 device vector (see bse.h)."""
+    return load_library().bse_apply_mixed(h, op, float(tile_tau), x_ptr, y_ptr)
+
+
 def bse_apply_noalloc(N, A_ptr, B_ptr, dtype, op, x_ptr, y_ptr, stream=0):
     """Allocation-free product from full device matrices (N <= BSE_NOALLOC_MAX_N)."""
     return load_library().bse_apply_noalloc(int(N), A_ptr, B_ptr, dtype, op, x_ptr, y_ptr, stream)
@@ -278,7 +286,7 @@ class Solver:
         self.nev = 0
 
     def solve(self, nev, tol=None, ncv=0, maxit=0, seed=0, vectors=True, lock_tol=0.0, check=True,
-              graphs=True, v0=None):
+              graphs=True, v0=None, tile_tau=0.0):
         torch = _torch()
         if tol is None:
             tol = 1e-12 if self.dtype == BSE_C128 else 1e-6
@@ -290,7 +298,7 @@ class Solver:
             bdt = torch.complex64 if self.dtype == BSE_C64 else torch.complex128
             v0t = torch.as_tensor(v0).to(device=self.device, dtype=bdt).contiguous()
         opts = bse_solve_opts(ncv=ncv, maxit=maxit, seed=seed, v0=v0t.data_ptr() if v0t is not None else None,
-                              lock_tol=lock_tol, stream_launches=0 if graphs else 1)
+                              lock_tol=lock_tol, stream_launches=0 if graphs else 1, tile_tau=tile_tau)
         rc, vals, nconv = bse_solve_ex(self.h, nev, tol, BSE_LOWEST, opts,
                                        ev.data_ptr() if ev is not None else None)
         if check:
@@ -373,12 +381,12 @@ class BatchedSolver:
                                     BSE_PH, self.dtype, BSE_DEVICE, self.stream.cuda_stream)
         self.As = self.Bs = None      # the library holds its own packed copies
 
-    def solve(self, nev, tol=1e-6, ncv=0, maxit=0, vectors=False, check=True, graphs=True):
+    def solve(self, nev, tol=1e-6, ncv=0, maxit=0, vectors=False, check=True, graphs=True, tile_tau=0.0):
         torch = _torch()
         vecs = [torch.empty((nev, 2 * n), dtype=self.cdtype, device=self.device) for n in self.Ns] \
             if vectors else None
         opts = bse_solve_opts(ncv=ncv, maxit=maxit, seed=0, v0=None, lock_tol=0.0,
-                              stream_launches=0 if graphs else 1)
+                              stream_launches=0 if graphs else 1, tile_tau=tile_tau)
         rc, vals, nconv = bse_solve_batched(self.h, len(self.Ns), nev, tol, BSE_LOWEST, opts,
                                             [v.data_ptr() for v in vecs] if vecs else None)
         if check:

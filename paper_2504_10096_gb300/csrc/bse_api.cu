@@ -29,6 +29,9 @@ struct ProbHost {
   void* B = nullptr;
   void* Ahl = nullptr;   // split tiles (BSE_C128_DF)
   void* Bhl = nullptr;
+  float* tmax = nullptr;   // mixed PH path: per-tile bound on |U|, |V| (device)
+  std::vector<float> htmax;
+  float tref = 0.f;        // the largest of them
   // solve buffers
   int ncv = 0;
   void *V = nullptr, *P = nullptr, *V2 = nullptr, *P2 = nullptr, *w = nullptr, *pw = nullptr;
@@ -90,6 +93,12 @@ struct bse_handle {
   std::vector<KState> hstate;
   TileJob* djobs = nullptr;
   int njobs = 0;
+  std::vector<TileJob> hjobs;
+  // mixed PH path: the tile jobs split by precision for the current solve
+  bool mixed = false;        // BSE_C64_MIXED with B
+  TileJob* djobs_fine = nullptr;
+  TileJob* djobs_coarse = nullptr;
+  int njobs_fine = 0, njobs_coarse = 0;
   int maxnT = 0;
   int64_t maxNpad = 0;
   int maxnrb = 1;
@@ -245,7 +254,10 @@ struct Driver {
       h->ev_used += 2;
       cudaEventRecord(e0, s);
     }
-    if (h->df)
+    if (h->mixed)
+      launch_product_mixed(h->dprobs, h->djobs_fine, h->njobs_fine, h->djobs_coarse, h->njobs_coarse, h->count,
+                           h->maxnT, mode, nullptr, shape, s);
+    else if (h->df)
       launch_product_df(h->dprobs, h->djobs, h->njobs, h->count, h->maxnT, mode, nullptr, h->ph != 0, h->split,
                         shape, s);
     else
@@ -623,9 +635,49 @@ int upload_probs(bse_handle* h) {
     d.st = h->dstate + i;
     d.Ahl = q.Ahl;
     d.Bhl = q.Bhl;
+    d.tmax = q.tmax;
   }
   CK(cudaMemcpyAsync(h->dprobs, h->hprobs.data(), sizeof(Prob) * h->count, cudaMemcpyHostToDevice,
                      h->stream));
+  return BSE_OK;
+}
+
+// Mixed PH path: split the tile jobs by precision for a solve at `tol`.  A
+// tile is "coarse" -- U, V rounded to FP32 and products accumulated on a
+// fixed-point grid (k_prod_tiles_mx) -- when its bound on |U|, |V| is at most
+// tau times the largest bound of its problem; the others ("fine") get exact
+// double-FP32 products (k_prod_tiles_df2).  The rounding of U, V on coarse
+// tiles is a fixed perturbation of at most 2^-24 tau max|U| per entry; with
+// random signs its 2-norm grows like 2 sqrt(N) times that, and the default
+// tau = min(2^-7, tol 2^24 / (16 sqrt(N))) keeps it near tol / 8 of the
+// largest entry.  tau < 0 puts every tile on the exact path.
+double default_tile_tau(double tol, int64_t N) {
+  return std::min(std::ldexp(1.0, -7), tol * std::ldexp(1.0, 24) / (16.0 * std::sqrt((double)N)));
+}
+
+int split_mixed_jobs(bse_handle* h, double tol, double tau_opt) {
+  std::vector<TileJob> fine, coarse;
+  fine.reserve(h->hjobs.size());
+  coarse.reserve(h->hjobs.size());
+  for (const TileJob& j : h->hjobs) {
+    const ProbHost& q = h->p[j.prob];
+    const double tau = tau_opt != 0.0 ? tau_opt : default_tile_tau(tol, q.N);
+    const bool exact = tau < 0.0 || !(q.htmax[j.t] <= tau * q.tref);
+    (exact ? fine : coarse).push_back(j);
+  }
+  if (!h->djobs_fine) {
+    int rc = dalloc((void**)&h->djobs_fine, sizeof(TileJob) * h->hjobs.size());
+    if (!rc) rc = dalloc((void**)&h->djobs_coarse, sizeof(TileJob) * h->hjobs.size());
+    if (rc) return rc;
+  }
+  h->njobs_fine = (int)fine.size();
+  h->njobs_coarse = (int)coarse.size();
+  if (!fine.empty())
+    CK(cudaMemcpyAsync(h->djobs_fine, fine.data(), sizeof(TileJob) * fine.size(), cudaMemcpyHostToDevice, h->stream));
+  if (!coarse.empty())
+    CK(cudaMemcpyAsync(h->djobs_coarse, coarse.data(), sizeof(TileJob) * coarse.size(), cudaMemcpyHostToDevice,
+                       h->stream));
+  CK(cudaStreamSynchronize(h->stream));    // the host vectors go out of scope
   return BSE_OK;
 }
 
@@ -658,6 +710,8 @@ int solve_impl(bse_handle* h, int nev, double tol, const bse_solve_opts* opts, d
   const bool graphs = !(opts && opts->stream_launches);
   int rc = alloc_solve(h, ncv);
   if (rc) return rc;
+  const double tau_opt = opts ? opts->tile_tau : 0.0;
+  if (h->mixed && (rc = split_mixed_jobs(h, tol, tau_opt))) return rc;
   h->ncv = ncv;
   h->nev = nev;
   h->solved = false;
@@ -733,15 +787,34 @@ int solve_impl(bse_handle* h, int nev, double tol, const bse_solve_opts* opts, d
   h->stats.shape_ctas_per_sm = h->shape.ctas_per_sm;
   h->stats.shape_strided = h->shape.strided;
   h->stats.tuned = h->tuned ? 1 : 0;
+  h->stats.tiles_fine = h->mixed ? h->njobs_fine : h->njobs;
+  h->stats.tiles_coarse = h->mixed ? h->njobs_coarse : 0;
+  h->stats.retried_exact = 0;
   h->solved = true;
+  // the rounded blocks of the coarse tiles are a fixed perturbation of the
+  // operator; if a pair then misses tol on the FP64 residual check (and not
+  // because of maxit), solve again with every tile on the exact path
+  if (h->mixed && h->njobs_coarse > 0 && worst == BSE_ENOCONV) {
+    bool maxit_hit = false;
+    for (const KState& s : h->hstate) maxit_hit |= s.steps >= s.maxit;
+    if (!maxit_hit) {
+      bse_solve_opts o{};
+      if (opts) o = *opts;
+      o.tile_tau = -1.0;
+      const int rc2 = solve_impl<ST>(h, nev, tol, &o, eval_out, evec_out, nconv_out);
+      h->stats.retried_exact = 1;
+      return rc2;
+    }
+  }
   return worst;
 }
 
 // candidate launch shapes of the handle's product kernel (see TuneKey)
 void setup_tuner(bse_handle* h) {
-  const int occ = h->df ? product_df_occupancy(h->ph != 0, h->split)
-                        : (h->vs == sizeof(float2) ? product_occupancy<float2, float>(h->ph != 0)
-                                                   : product_occupancy<double2, double>(h->ph != 0));
+  const int occ = h->mixed ? product_mx_occupancy()
+                 : h->df  ? product_df_occupancy(h->ph != 0, h->split)
+                          : (h->vs == sizeof(float2) ? product_occupancy<float2, float>(h->ph != 0)
+                                                     : product_occupancy<double2, double>(h->ph != 0));
   const bool batch = h->count > 1;
   h->cands.clear();
   for (int c = 1; c <= occ; ++c) {
@@ -1154,6 +1227,7 @@ int bse_create_batched(int count, const int64_t* N, const void* const* A, const 
   h->df = dtype == BSE_C128_DF || dtype == BSE_C64_MIXED;
   h->split = dtype == BSE_C128_DF;
   h->tiles64 = is_c64(dtype);
+  h->mixed = dtype == BSE_C64_MIXED && form == BSE_PH;
   h->es = is_c64(dtype) ? sizeof(float2) : sizeof(double2);   // stored (tile / caller) elements
   h->vs = dtype == BSE_C64 ? sizeof(float2) : sizeof(double2);  // Krylov vectors
   h->stream = (cudaStream_t)stream;
@@ -1195,6 +1269,17 @@ int bse_create_batched(int count, const int64_t* N, const void* const* A, const 
           launch_split_tiles((const double2*)q.B, nel, (float4*)q.Bhl, h->stream);
       }
     }
+    if (!rc && dtype == BSE_C64_MIXED && h->ph) {
+      if (!(rc = dalloc((void**)&q.tmax, sizeof(float) * (size_t)q.ntiles))) {
+        launch_tile_bound((const float2*)q.A, (const float2*)q.B, q.ntiles, q.tmax, h->stream);
+        q.htmax.resize(q.ntiles);
+        if (cudaMemcpyAsync(q.htmax.data(), q.tmax, sizeof(float) * q.ntiles, cudaMemcpyDeviceToHost, h->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+          rc = BSE_ECUDA;
+        for (float v : q.htmax) q.tref = std::max(q.tref, v);
+      }
+    }
     for (int I = 0; I < q.nT; ++I)
       for (int J = I; J < q.nT; ++J) {
         TileJob t;
@@ -1206,6 +1291,7 @@ int bse_create_batched(int count, const int64_t* N, const void* const* A, const 
       }
   }
   if (rc == BSE_OK && jobs.size() > 2147483647ull) rc = BSE_EINVAL;
+  if (rc == BSE_OK && h->mixed) h->hjobs = jobs;
   if (rc == BSE_OK) {
     h->njobs = (int)jobs.size();
     rc = dalloc((void**)&h->djobs, sizeof(TileJob) * jobs.size());
@@ -1276,6 +1362,34 @@ int bse_apply(bse_handle* h, int op, int k, const void* X, void* Y) {
   return apply_impl<double2>(h, op, k, X, Y);
 }
 
+int bse_apply_mixed(bse_handle* h, int op, double tile_tau, const void* X, void* Y) {
+  if (!h || !X || !Y || h->count != 1 || !h->mixed) return BSE_EINVAL;
+  if (op != BSE_OP_MPLUS && op != BSE_OP_MMINUS) return BSE_EINVAL;
+  if (!std::isfinite(tile_tau)) return BSE_EINVAL;
+  ProbHost& q = h->p[0];
+  int rc;
+  if (!q.w || q.ncv == 0) {
+    if ((rc = alloc_solve(h, std::min<int64_t>(q.N, 8) > 1 ? (int)std::min<int64_t>(q.N, 8) : 1))) return rc;
+  }
+  if ((rc = upload_probs(h))) return rc;
+  if ((rc = split_mixed_jobs(h, 1e-6, tile_tau))) return rc;
+  count_launch();
+  k_pad_in<double2><<<dim3((unsigned)((q.Npad + 255) / 256), 1), 256, 0, h->stream>>>(
+      (const double2*)X, q.N, q.N, q.Npad, 1, 0, (double2*)q.w);
+  GenericIO io{};
+  io.xa = q.w;
+  io.y = q.pw;
+  io.sB = op == BSE_OP_MPLUS ? 1.0 : -1.0;
+  launch_product_mixed(h->dprobs, h->djobs_fine, h->njobs_fine, h->djobs_coarse, h->njobs_coarse, 1, h->maxnT,
+                       PM_GENERIC, &io, h->shape, h->stream);
+  CK(cudaMemcpyAsync(Y, q.pw, sizeof(double2) * (size_t)q.N, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  h->stats.tiles_fine = h->njobs_fine;
+  h->stats.tiles_coarse = h->njobs_coarse;
+  return BSE_OK;
+}
+
 int bse_haydock(bse_handle* h, const void* d, int where, int m, int sign, int nw, const double* omega, double eta,
                 double* spectrum_out, double* response_out, double* coef_out, int* steps_out) {
   if (!h || !d || !omega || !spectrum_out || h->count != 1) return BSE_EINVAL;
@@ -1318,7 +1432,10 @@ int bse_destroy(bse_handle* h) {
     dfree(q.B);
     dfree(q.Ahl);
     dfree(q.Bhl);
+    dfreet(q.tmax);
   }
+  dfreet(h->djobs_fine);
+  dfreet(h->djobs_coarse);
   dfreet(h->dprobs);
   dfreet(h->dstate);
   dfreet(h->djobs);

@@ -118,6 +118,9 @@ struct Prob {
   // (hi, lo) float pairs, float4 {re_hi, im_hi, re_lo, im_lo} per element
   const void* Ahl;
   const void* Bhl;
+  // complex64 PH handles on the mixed path: per tile, an upper bound on every
+  // |U|, |V| component (U, V = A +- B), indexed like the packed tiles
+  const float* tmax;
 };
 
 // Jobs of the tiled product: problem, tile row I, tile column J, tile index.
@@ -187,6 +190,14 @@ void launch_product_df(const Prob* dprobs, const TileJob* jobs, int njobs, int n
                        int mode, const GenericIO* io_host, bool hasB, bool split, ProdShape shape,
                        cudaStream_t s);
 void launch_split_tiles(const double2* packed, int64_t nelem, float4* split, cudaStream_t s);
+// mixed path (complex64 PH tiles, FP64 vectors): exact double-FP32 products on the
+// "fine" tiles (k_prod_tiles_df2), fixed-point-grid accumulation with rounded U, V on
+// the "coarse" ones (k_prod_tiles_mx), then the FP64 reduction (k_product_df.cu)
+void launch_product_mixed(const Prob* dprobs, const TileJob* fine, int nfine, const TileJob* coarse, int ncoarse,
+                          int nprob, int maxnT, int mode, const GenericIO* io_host, ProdShape shape, cudaStream_t s);
+int product_mx_occupancy();
+// per-tile bound max(|A_re| + |B_re|, |A_im| + |B_im|) of complex64 tiles (k_product_df.cu)
+void launch_tile_bound(const float2* A, const float2* B, int64_t ntiles, float* out, cudaStream_t s);
 void launch_prod_reduce_d(const Prob* dprobs, int nprob, int maxnT, int mode, GenericIO io, cudaStream_t s);
 
 // bounded-wait self-test (k_adjoint_tc.cu): 0 on success, -1 on a CUDA error

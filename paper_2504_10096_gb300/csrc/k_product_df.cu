@@ -17,6 +17,8 @@
 //
 // The Krylov basis, Gram-Schmidt, projected problem and the final residuals
 // of this path stay in FP64; only the streaming product changes arithmetic.
+#include <algorithm>
+
 #include "bse_internal.cuh"
 
 namespace bse {
@@ -479,6 +481,220 @@ k_prod_tiles_df2(const Prob* __restrict__ probs, const TileJob* __restrict__ job
   }
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-path product on "coarse" tiles (complex64 PH tiles whose entries are
+// small against the largest tile of the problem): the same real form, but
+// (1) U = A + sB and V = A - sB are rounded to FP32 -- a fixed perturbation of
+//     the operator of at most 2^-24 |U| per entry, consistent between the
+//     passes (it is the operator of the rounded blocks), and allowed only on
+//     tiles whose entries are a small fraction tau of the largest ones;
+// (2) every product of U with the double-FP32 vector x = xh + xl is
+//     accumulated on a fixed-point grid: each chain starts at sigma = 1.5 2^e
+//     with 2^(e-1) above the largest partial sum the chain can reach (from the
+//     tile's bound on |U| and the staged chunk's max |xh|), so the chain value
+//     H = sigma + S stays in [2^e, 2^(e+1)) and every
+//         t = fma(U, xh, H)   (H + U xh rounded to the grid 2^(e-23))
+//         d = t - H           (exact: both on the grid, |d| < 2^e)
+//         r = fma(U, xh, -d)  (U xh - d, |r| <= 2^(e-24), rounded at 2^(e-48))
+//     moves the part of the product below the grid into a plain FP32 tail L,
+//     with U xl added there too (ExtractScalar-style splitting, Rump, Ogita
+//     and Oishi, "Accurate floating-point summation", 2008, used here as an
+//     accumulator).  Five packed f32x2 instructions per pair of
+//     multiply-accumulates, against twelve for Dekker's product and Knuth's
+//     TwoSum in k_prod_tiles_df2; the chain error is about 2^-35 of
+//     max|U| max|xh| (the tail's own FP32 rounding), so tiles with big
+//     entries stay on k_prod_tiles_df2.
+// Row and column chain results leave as normalised double-FP32 pairs and go
+// through the same cross-lane reduction and FP64 partial-sum slots as the
+// other double-FP32 kernels.
+__device__ __forceinline__ float grid_sigma(float m, int headroom) {
+  // 1.5 2^e with e = exponent(m) + headroom; m >= 0 (0 for an all-zero operand)
+  int e = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127 + headroom;
+  e = max(-100, min(e, 120));
+  return __uint_as_float(((unsigned)(e + 127) << 23) | 0x400000u);
+}
+
+struct XMix { f2 h1, l1, h2, l2; };   // hi / lo of the two operand pairings of one vector entry
+
+__device__ __forceinline__ XMix xmix(double2 v, bool row) {
+  const float4 s = split_d(v);           // {re_hi, im_hi, re_lo, im_lo}
+  XMix o;
+  o.h1 = pk(s.x, s.y);
+  o.l1 = pk(s.z, s.w);
+  if (!row) {                            // column block x_J: (re, -im)
+    o.h2 = pk(s.x, -s.y);
+    o.l2 = pk(s.z, -s.w);
+  } else {                               // row block x_I: (im, -re)
+    o.h2 = pk(s.y, -s.x);
+    o.l2 = pk(s.w, -s.z);
+  }
+  return o;
+}
+
+// (H, L) += u (xh + xl) on the grid of H (see above), lane-wise
+__device__ __forceinline__ void gacc(f2& H, f2& L, f2 u, f2 xh, f2 xl) {
+  const f2 t = fma2(u, xh, H);
+  const f2 nd = sub2(H, t);               // -(t - H), exact
+  const f2 r = fma2(u, xh, nd);           // u xh - (t - H)
+  L = add2(L, r);
+  L = fma2(u, xl, L);
+  H = t;
+}
+
+__device__ __forceinline__ void two_sum1(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+__global__ void __launch_bounds__(PROD_THREADS, 2)
+k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs, int njobs, int mode,
+                GenericIO io, int strided) {
+  __shared__ XMix xc[TS], xr[TS];
+  __shared__ DFC rpark[8][PROD_THREADS];
+  __shared__ float smax[8];
+  DFC(*red)[TS] = reinterpret_cast<DFC(*)[TS]>(&rpark[0][0]);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int per = strided ? 1 : (njobs + gridDim.x - 1) / gridDim.x;
+  const int t0 = strided ? blockIdx.x : blockIdx.x * per;
+  const int t1 = strided ? njobs : min(njobs, t0 + per);
+  const int dt = strided ? gridDim.x : 1;
+  const f2 zero = pk(0.f, 0.f);
+  for (int t = t0; t < t1; t += dt) {
+    const TileJob jb = jobs[t];
+    const Prob& p = probs[jb.prob];
+    const double2* x;
+    double sB;
+    if (!df_operands(p, mode, io, x, sB)) continue;   // uniform per CTA
+    const bool diag = jb.I == jb.J;
+    __syncthreads();
+    float mx;
+    {
+      const int r = tid & (TS - 1);
+      const double2 v = x[(int64_t)(tid < TS ? jb.J : jb.I) * TS + r];
+      const XMix o = xmix(v, tid >= TS);
+      if (tid < TS) xc[r] = o;
+      else xr[r] = o;
+      float a0, a1;
+      upk(o.h1, a0, a1);
+      mx = fmaxf(fabsf(a0), fabsf(a1));
+#pragma unroll
+      for (int m = 16; m >= 1; m >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, m));
+      if ((tid & 31) == 0) smax[tid >> 5] = mx;
+    }
+    __syncthreads();
+    mx = smax[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) mx = fmaxf(mx, smax[w]);
+    // bound on every |U xh| of this tile; row chains sum 8 such products per lane,
+    // column chains 16; one more bit absorbs the roundings of U, of the bound and
+    // of the grid itself
+    const float m = p.tmax[jb.t] * mx;
+    const float sgr = grid_sigma(m, 6), sgc = grid_sigma(m, 7);
+    const f2 sr2 = pk(sgr, sgr), sc2 = pk(sgc, sgc);
+    const float2* At = (const float2*)p.A + (int64_t)jb.t * (TS * TS);
+    const float2* Bt = (const float2*)p.B + (int64_t)jb.t * (TS * TS);
+    const float sg = sB > 0.0 ? 1.f : -1.f;
+    const f2 spm = pk(sg, -sg);
+    f2 cH[8], cL[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      cH[b] = sc2;
+      cL[b] = zero;
+    }
+    float2 av[8], bv[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      av[b] = __ldg(At + ty * TS + tx + 16 * b);
+      bv[b] = __ldg(Bt + ty * TS + tx + 16 * b);
+    }
+#pragma unroll 1
+    for (int a = 0; a < 8; ++a) {
+      const int r = ty + 16 * a;
+      float2 an[8], bn[8];
+      if (a < 7) {                          // the next row's elements are in flight meanwhile
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          an[b] = __ldg(At + (r + 16) * TS + tx + 16 * b);
+          bn[b] = __ldg(Bt + (r + 16) * TS + tx + 16 * b);
+        }
+      }
+      const XMix y = xr[r];
+      f2 H1 = sr2, L1 = zero, H2 = sr2, L2 = zero;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const XMix xv = xc[tx + 16 * b];
+        // (U_re, V_re) and (U_im, V_im), rounded
+        const f2 uvr = fma2(pk(bv[b].x, bv[b].x), spm, pk(av[b].x, av[b].x));
+        const f2 uvi = fma2(pk(bv[b].y, bv[b].y), spm, pk(av[b].y, av[b].y));
+        gacc(H1, L1, uvr, xv.h1, xv.l1);
+        gacc(H2, L2, uvi, xv.h2, xv.l2);
+        if (!diag) {
+          gacc(cH[b], cL[b], uvr, y.h1, y.l1);
+          gacc(cH[b], cL[b], uvi, y.h2, y.l2);
+        }
+      }
+      // y_re = lane 0 of chain 1 + lane 1 of chain 2, y_im = lane 1 of 1 + lane 0 of 2;
+      // the grid parts add exactly, then (grid, tail) is normalised
+      const f2 S1 = sub2(H1, sr2), S2 = sub2(H2, sr2);
+      float s1a, s1b, s2a, s2b, l1a, l1b, l2a, l2b;
+      upk(S1, s1a, s1b);
+      upk(S2, s2a, s2b);
+      upk(L1, l1a, l1b);
+      upk(L2, l2a, l2b);
+      DFC ra;
+      two_sum1(__fadd_rn(s1a, s2b), __fadd_rn(l1a, l2b), ra.rh, ra.rl);
+      two_sum1(__fadd_rn(s1b, s2a), __fadd_rn(l1b, l2a), ra.ih, ra.il);
+      rpark[a][tid] = ra;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        av[b] = an[b];
+        bv[b] = bn[b];
+      }
+    }
+    DFC racc[8], cacc[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      float hr, hi, lr, li;
+      upk(sub2(cH[b], sc2), hr, hi);
+      upk(cL[b], lr, li);
+      two_sum1(hr, lr, cacc[b].rh, cacc[b].rl);
+      two_sum1(hi, li, cacc[b].ih, cacc[b].il);
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) racc[a] = rpark[a][tid];
+    __syncthreads();   // rpark is reused below as the column-reduction buffer
+    df_tile_reduce(racc, cacc, red, diag, p, jb);
+  }
+}
+
+// per-tile bound max over the tile of max(|A_re| + |B_re|, |A_im| + |B_im|)
+// (>= every |U| and |V| component for s = +-1); one CTA per tile
+__global__ void __launch_bounds__(256)
+k_tile_bound(const float2* __restrict__ A, const float2* __restrict__ B, int64_t ntiles, float* __restrict__ out) {
+  __shared__ float sm[8];
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const float2* a = A + t * (TS * TS);
+    const float2* b = B + t * (TS * TS);
+    float m = 0.f;
+    for (int e = threadIdx.x; e < TS * TS; e += 256) {
+      const float2 x = a[e], y = b[e];
+      m = fmaxf(m, fmaxf(fabsf(x.x) + fabsf(y.x), fabsf(x.y) + fabsf(y.y)));
+    }
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, s));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float r = sm[0];
+      for (int w = 1; w < 8; ++w) r = fmaxf(r, sm[w]);
+      // one ulp up: the sums above were rounded to nearest
+      out[t] = r > 0.f ? __uint_as_float(__float_as_uint(r) + 1u) : 0.f;
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_split_tiles(const double2* __restrict__ in, int64_t n, float4* __restrict__ out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = split_d(in[i]);
@@ -531,6 +747,41 @@ void launch_product_df(const Prob* dprobs, const TileJob* jobs, int njobs, int n
     else launch_df<false, false>(dprobs, jobs, njobs, mode, io, shape, s);
   }
   launch_prod_reduce_d(dprobs, nprob, maxnT, mode, io, s);
+}
+
+int product_mx_occupancy() {
+  static int occ = 0;
+  if (!occ) {
+    int o = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_prod_tiles_mx, PROD_THREADS, 0);
+    occ = o > 0 ? o : 1;
+  }
+  return occ;
+}
+
+void launch_product_mixed(const Prob* dprobs, const TileJob* fine, int nfine, const TileJob* coarse, int ncoarse,
+                          int nprob, int maxnT, int mode, const GenericIO* io_host, ProdShape shape, cudaStream_t s) {
+  GenericIO io{};
+  if (io_host) io = *io_host;
+  if (nfine > 0) {
+    count_launch();
+    const ProdShape fs{0, 1};
+    k_prod_tiles_df2<<<product_grid(df_occupancy<true, false>(), fs, nfine), PROD_THREADS, 0, s>>>(
+        dprobs, fine, nfine, mode, io, 1);
+  }
+  if (ncoarse > 0) {
+    count_launch();
+    k_prod_tiles_mx<<<product_grid(product_mx_occupancy(), shape, ncoarse), PROD_THREADS, 0, s>>>(
+        dprobs, coarse, ncoarse, mode, io, shape.strided);
+  }
+  count_launch();
+  launch_prod_reduce_d(dprobs, nprob, maxnT, mode, io, s);
+}
+
+void launch_tile_bound(const float2* A, const float2* B, int64_t ntiles, float* out, cudaStream_t s) {
+  count_launch();
+  const int grid = (int)std::min<int64_t>(ntiles, 4096);
+  k_tile_bound<<<grid, 256, 0, s>>>(A, B, ntiles, out);
 }
 
 void launch_split_tiles(const double2* packed, int64_t nelem, float4* split, cudaStream_t s) {

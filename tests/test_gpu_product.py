@@ -105,3 +105,40 @@ def test_apply_df64_products(n):
         # double-FP32 terms carry 2^-48 relative error (the dropped lo x lo product)
         assert_elementwise(Y, ref, product_bound(A, B, X, name), 2.0 ** -48, C_ELEM, f"df op {name}")
     s.close()
+
+
+@pytest.mark.parametrize("n", [129, 515])
+def test_mixed_product_exact_and_coarse_tiles(n):
+    """The mixed path's product (bse_apply_mixed, complex128 vectors) on a
+    complex64 handle.  Every tile exact (tile_tau < 0, double-FP32): within a
+    few 2^-48 of |M||x| per entry of the oracle's M+/M- x.  Every tile coarse
+    (tile_tau = 1): U = A + sB, V = A - sB rounded to FP32 on purpose, so the
+    reference is the real form of Eq. 5 applied with those rounded blocks in
+    FP64; the fixed-point-grid accumulation must match it to 2^-30 of the
+    largest |U||x| row sum (plain FP32 accumulation would be near 2^-22)."""
+    from paper_2504_10096_gb300 import bse
+    A, B = problem(n, "c64", seed=n + 21)
+    s = bse.Solver(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), mixed=True)
+    x = rand_block(n, 1, "c128", seed=9)
+    xt = torch.from_numpy(x[:, 0]).cuda()
+    A64, B64 = A.astype(np.complex128), B.astype(np.complex128)
+    for op, sgn, fn in ((bse.BSE_OP_MPLUS, 1.0, O.apply_mplus), (bse.BSE_OP_MMINUS, -1.0, O.apply_mminus)):
+        y = torch.empty_like(xt)
+        assert bse.bse_apply_mixed(s.h, op, -1.0, xt.data_ptr(), y.data_ptr()) == bse.BSE_OK
+        assert s.stats()["tiles_coarse"] == 0
+        ref = fn(A64, B64, x)
+        assert_elementwise(y.cpu().numpy()[:, None], ref, product_bound(A, B, x, "mplus"), 2.0 ** -48, 64,
+                           f"mixed exact, sign {sgn}")
+        assert bse.bse_apply_mixed(s.h, op, 1.0, xt.data_ptr(), y.data_ptr()) == bse.BSE_OK
+        assert s.stats()["tiles_fine"] == 0 and s.stats()["tiles_coarse"] > 0
+        f32 = np.float32
+        ure = (A.real.astype(f32) + f32(sgn) * B.real.astype(f32)).astype(np.float64)
+        uim = (A.imag.astype(f32) + f32(sgn) * B.imag.astype(f32)).astype(np.float64)
+        vre = (A.real.astype(f32) - f32(sgn) * B.real.astype(f32)).astype(np.float64)
+        vim = (A.imag.astype(f32) - f32(sgn) * B.imag.astype(f32)).astype(np.float64)
+        xr, xi = x[:, 0].real, x[:, 0].imag
+        emu = (ure @ xr - vim @ xi) + 1j * (uim @ xr + vre @ xi)
+        scale = np.max((np.abs(ure) + np.abs(vim) + np.abs(uim) + np.abs(vre)) @ np.abs(x[:, 0]))
+        err = np.max(np.abs(y.cpu().numpy() - emu))
+        assert err <= 2.0 ** -30 * scale, (sgn, err / scale)
+    s.close()

@@ -249,8 +249,11 @@ def run_gpu(args):
     peaks, peak_kind = _peaks()
     ingest_bytes = 2 * N * N * 16 + 2 * (N * (N + 1) / 2) * 16
     clocks = clk.summary()
-    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp64_peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12        # TFLOP/s: 152 SMs x 2 FP64 FMA/clk x 2 flops
+    # FP64 FMA peak measured on this GPU (libbse's dependent-free FMA kernel, CUDA events),
+    # sampled clocks beside it
+    with ClockSampler(torch.cuda.current_device()) as clk64:
+        fp64_peak, fp64_ms = bse.bse_measure_fp64_peak(1 << 18)
+    clocks64 = clk64.summary()
     achieved_tf = per_launch_flops / t_launch / 1e12
     achieved_gbs = per_launch_bytes / t_launch / 1e9
     # ---- adjoint (a10) and e2e through host buffers (rank-local)
@@ -297,6 +300,8 @@ def run_gpu(args):
                    "s_per_solve": t_df, "krylov_steps": sd["steps"], "max_residual": sd["max_residual"],
                    "product_GBs": per_launch_bytes / (sd["ms_product"] / sd["passes"] * 1e-3) / 1e9,
                    "max_rel_err_vs_oracle": float(np.max(np.abs(vdf - gold) / gold)) if gold is not None else None}
+    # ---- the metric's own configuration: config 4, mixed vs plain FP64 at residual <= 1e-6
+    c4 = config4_record(args, stream) if not args.skip_config4 else None
     if rank != 0:
         return
     cpu_v, cpu_raw = cpu_baseline_sample()
@@ -318,7 +323,9 @@ def run_gpu(args):
                 "frac": achieved_tf / fp64_peak, "traffic": traffic,
                 "algorithmic_bytes": per_launch_bytes,
                 "kernel": "k_prod_tiles + k_prod_reduce (one folded product M+/M- over packed A and B)",
-                "peak_note": "FP64 FMA peak from 152 SMs x 2 FP64 FMA/clk/SM x 2 flops x median SM clock",
+                "peak_note": "FP64 FMA peak measured in this run (bse_measure_fp64_peak: 8 independent FMA "
+                             f"chains per thread on every SM, {fp64_ms:.1f} ms launch, CUDA events)",
+                "peak_kind": "measured", "peak_clocks": clocks64,
                 "achieved_hbm_gbs": achieved_gbs, "hbm_peak_gbs": peaks.get("hbm_gbs"),
                 "hbm_frac": achieved_gbs / peaks.get("hbm_gbs", 6800.0), "hbm_peak_kind": peak_kind}
     line = {
@@ -348,8 +355,65 @@ def run_gpu(args):
                    "GBs": ingest_bytes / statistics.median(ingest_ms) / 1e6,
                    "hbm_frac": ingest_bytes / statistics.median(ingest_ms) / 1e6 / peaks.get("hbm_gbs", 6800.0)},
         "variant_df_products": variant,
+        "config4": c4,
     }
     print(json.dumps(line), flush=True)
+
+
+def config4_record(args, stream):
+    """Config 4 (PH, N = 50000, complex64 A and B, energies U[1, 12] eV, N_G = 2000,
+    lowest 200, tol 1e-6): one solve on the mixed path (complex64 storage, FP64 basis,
+    exact or grid-accumulated double-FP32 products) and one on the plain FP64 path
+    (the same complex64 values promoted to complex128), each timed with CUDA events on
+    the library's stream, with steps, passes, max FP64 residual, eigenvalue agreement,
+    the speed-up and the mixed product's bandwidth."""
+    import torch
+    from paper_2504_10096_gb300 import bse
+    from synthetic import CONFIGS, make_problem_torch
+    spec = CONFIGS[4]
+    N, nev, tol = spec.n, spec.nev, 1e-6
+    p = make_problem_torch(spec, device="cuda")
+    A, B = p["A"], p["B"]
+    del p
+    torch.cuda.synchronize()
+    out = {"workload": f"config 4: PH N={N} (H {2 * N}), complex64 A and B, energies U[1,12] eV, N_G=2000, "
+                       f"lowest {nev}, tol {tol:g}", "data": "synthetic (device generator)"}
+    peaks, _ = _peaks()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        s = bse.Solver(A, B, stream=stream, mixed=True)
+        vm, _, nm, tm = _timed_solve(s, nev, tol, stream, vectors=False)
+        st = s.stats()
+        s.close()
+    pass_ms = st["ms_product"] / max(st["passes"], 1)
+    pbytes = 2 * (N * (N + 1) / 2) * 8 + 3 * N * 16
+    out["mixed"] = {"s": tm, "krylov_steps": st["steps"], "passes": st["passes"], "restarts": st["restarts"],
+                    "nconv": int(nm), "max_residual": st["max_residual"], "tiles_fine": st["tiles_fine"],
+                    "tiles_coarse": st["tiles_coarse"], "retried_exact": st["retried_exact"],
+                    "product_ms_per_pass": pass_ms, "product_share": st["ms_product"] / (tm * 1e3),
+                    "product_GBs": pbytes / pass_ms / 1e6,
+                    "product_hbm_frac": pbytes / pass_ms / 1e6 / peaks.get("hbm_gbs", 6800.0),
+                    "clocks": clk.summary()}
+    if args.config4_fp64:
+        A64 = A.to(torch.complex128)
+        del A
+        B64 = B.to(torch.complex128)
+        del B
+        torch.cuda.synchronize()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            s = bse.Solver(A64, B64, stream=stream)
+            del A64, B64
+            v64, _, n64, t64 = _timed_solve(s, nev, tol, stream, vectors=False)
+            st = s.stats()
+            s.close()
+        out["fp64"] = {"s": t64, "krylov_steps": st["steps"], "passes": st["passes"], "restarts": st["restarts"],
+                       "nconv": int(n64), "max_residual": st["max_residual"],
+                       "product_ms_per_pass": st["ms_product"] / max(st["passes"], 1), "clocks": clk.summary()}
+        out["max_rel_eig_diff_mixed_vs_fp64"] = float(np.max(np.abs(vm - v64) / v64))
+        out["speedup_mixed_over_fp64"] = t64 / tm
+    else:
+        del A, B
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_product(args):
@@ -636,6 +700,10 @@ def main():
     ap.add_argument("--fp32", action="store_true", help="mixed mode: also run plain FP32 (BSE_C64)")
     ap.add_argument("--mixed", action="store_true",
                     help="product mode: complex64 storage with the mixed path's products (BSE_C64_MIXED)")
+    ap.add_argument("--skip-config4", action="store_true",
+                    help="solve mode: leave out the config-4 record (mixed vs FP64 at N = 50000)")
+    ap.add_argument("--no-config4-fp64", dest="config4_fp64", action="store_false",
+                    help="solve mode: config-4 record without its plain FP64 leg")
     ap.add_argument("--tau", type=float, default=0.0,
                     help="product mode with --mixed: tile threshold (0: the tol-1e-6 default, <0: every tile exact)")
     ap.add_argument("--ncv", type=int, default=0, help="solve mode: Krylov subspace size (0 = library default)")

@@ -375,6 +375,16 @@ int bse_selftest_bounded_wait(int arrive, int* expired);
    BSE_ESTATE before the first solve, BSE_EINVAL for bad arguments. */
 int bse_get_residuals(const bse_handle* h, int problem, double* res_out, int n);
 
+/*
+ * bse_measure_fp64_peak -- FP64 FMA throughput of the current device, for the
+ * roofline of the FP64 path (whose structured product is bound by the FP64
+ * pipe on this GPU).  One launch of `iters` iterations of 8 independent FMA
+ * chains per thread on every SM, timed with CUDA events after a warm-up;
+ * *tflops_out = 2 x FMAs / time.  The paper has no counterpart.  Allocates a
+ * small output buffer; BSE_EINVAL for iters outside [1, 2^24].
+ */
+int bse_measure_fp64_peak(int iters, double* tflops_out, double* ms_out);
+
 /* Counters of the last solve or spectrum (single-problem handles; for
    batched handles the sums over problems). */
 int bse_get_stats(const bse_handle* h, bse_stats* out);

@@ -28,7 +28,7 @@ BSE_OP_A, BSE_OP_MPLUS, BSE_OP_MMINUS, BSE_OP_H = 0, 1, 2, 3
 EXPORTED = ["bse_strerror", "bse_create", "bse_create_batched", "bse_solve", "bse_solve_ex",
             "bse_solve_batched", "bse_backward", "bse_apply", "bse_get_stats", "bse_destroy",
             "bse_apply_noalloc", "bse_backward_ex", "bse_haydock", "bse_selftest_bounded_wait",
-            "bse_get_residuals", "bse_apply_mixed"]
+            "bse_get_residuals", "bse_apply_mixed", "bse_measure_fp64_peak"]
 BSE_IMPL_AUTO, BSE_IMPL_CUDA_CORES, BSE_IMPL_TENSOR_CORES = 0, 1, 2
 BSE_NOALLOC_MAX_N = 4096
 
@@ -85,6 +85,7 @@ def load_library(path: str | None = None):
     lib.bse_get_stats.argtypes = [H, ctypes.POINTER(bse_stats)]
     lib.bse_get_residuals.argtypes = [H, c_int, ctypes.POINTER(c_dbl), c_int]
     lib.bse_apply_mixed.argtypes = [H, c_int, c_dbl, c_vp, c_vp]
+    lib.bse_measure_fp64_peak.argtypes = [c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl)]
     lib.bse_destroy.argtypes = [H]
     lib.bse_apply_noalloc.argtypes = [c_i64, c_vp, c_vp, c_int, c_int, c_vp, c_vp, c_vp]
     lib.bse_backward_ex.argtypes = [H, ctypes.POINTER(c_dbl), c_int, c_vp, c_vp, c_int]
@@ -207,6 +208,14 @@ def bse_get_residuals(h, n, problem=0):
     r = (ctypes.c_double * max(n, 1))()
     _check(load_library().bse_get_residuals(h, int(problem), r, int(n)), "bse_get_residuals")
     return np.array(r[:n], dtype=np.float64)
+
+
+def bse_measure_fp64_peak(iters=1 << 16):
+    """Measured FP64 FMA rate of the current device (TFLOP/s, ms of the timed launch)."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load_library().bse_measure_fp64_peak(int(iters), ctypes.byref(tf), ctypes.byref(ms)),
+           "bse_measure_fp64_peak")
+    return tf.value, ms.value
 
 
 def bse_destroy(h):

@@ -36,6 +36,8 @@ struct ProbHost {
   int ncv = 0;
   void *V = nullptr, *P = nullptr, *V2 = nullptr, *P2 = nullptr, *w = nullptr, *pw = nullptr;
   void* part = nullptr;
+  void* xs = nullptr;        // mixed PH path: pre-split product vector and chunk maxima
+  float* xmax = nullptr;
   double *cpart = nullptr, *coef = nullptr, *small = nullptr, *S = nullptr;
   // results
   double2* Z = nullptr;
@@ -117,6 +119,7 @@ struct bse_handle {
   void* adj_panels = nullptr;
   size_t adj_panel_bytes = 0;
   int* adj_err = nullptr;
+  int* prod_err = nullptr;   // raised by a product kernel whose bounded wait expired
   double* gdev = nullptr;
   // product timing ring
   std::vector<cudaEvent_t> ev;
@@ -172,7 +175,8 @@ void dfreet(T*& ptr) {
 bool is_c64(int dtype) { return dtype == BSE_C64 || dtype == BSE_C64_MIXED; }
 
 void free_solve_buffers(ProbHost& q) {
-  dfree(q.V); dfree(q.P); dfree(q.V2); dfree(q.P2); dfree(q.w); dfree(q.pw); dfree(q.part);
+  dfree(q.V); dfree(q.P); dfree(q.V2); dfree(q.P2); dfree(q.w); dfree(q.pw); dfree(q.part); dfree(q.xs);
+  dfreet(q.xmax);
   dfreet(q.cpart); dfreet(q.coef); dfreet(q.small); dfreet(q.S);
   q.ncv = 0;
 }
@@ -256,7 +260,7 @@ struct Driver {
     }
     if (h->mixed)
       launch_product_mixed(h->dprobs, h->djobs_fine, h->njobs_fine, h->djobs_coarse, h->njobs_coarse, h->count,
-                           h->maxnT, mode, nullptr, shape, s);
+                           h->maxnT, mode, nullptr, shape, h->prod_err, s);
     else if (h->df)
       launch_product_df(h->dprobs, h->djobs, h->njobs, h->count, h->maxnT, mode, nullptr, h->ph != 0, h->split,
                         shape, s);
@@ -448,10 +452,12 @@ struct Driver {
   int read_state() {
     CK(cudaMemcpyAsync(h->hstate.data(), h->dstate, sizeof(KState) * h->count, cudaMemcpyDeviceToHost,
                        h->stream));
+    int perr = 0;
+    if (h->prod_err) CK(cudaMemcpyAsync(&perr, h->prod_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     CK(cudaGetLastError());
     harvest_events();
-    return BSE_OK;
+    return perr ? BSE_ETIMEOUT : BSE_OK;
   }
 
   int iterate(uint64_t seed, const void* v0) {
@@ -594,6 +600,10 @@ int alloc_solve(bse_handle* h, int ncv) {
     if ((rc = dalloc(&q.w, es * (size_t)q.Npad))) return rc;
     if ((rc = dalloc(&q.pw, es * (size_t)q.Npad))) return rc;
     if ((rc = dalloc(&q.part, cs * (size_t)q.nT * q.nT * TS))) return rc;
+    if (h->mixed) {
+      if ((rc = dalloc(&q.xs, 64 * (size_t)q.Npad))) return rc;
+      if ((rc = dalloc((void**)&q.xmax, sizeof(float) * (size_t)q.nT))) return rc;
+    }
     if ((rc = dalloc((void**)&q.cpart, sizeof(double2) * (size_t)nrb * ncol))) return rc;
     if ((rc = dalloc((void**)&q.coef, sizeof(double2) * 2 * (size_t)ncol))) return rc;
     if ((rc = dalloc((void**)&q.small, sizeof(double) * 6 * (size_t)(ncv + 1)))) return rc;
@@ -636,6 +646,8 @@ int upload_probs(bse_handle* h) {
     d.Ahl = q.Ahl;
     d.Bhl = q.Bhl;
     d.tmax = q.tmax;
+    d.xs = q.xs;
+    d.xmax = q.xmax;
   }
   CK(cudaMemcpyAsync(h->dprobs, h->hprobs.data(), sizeof(Prob) * h->count, cudaMemcpyHostToDevice,
                      h->stream));
@@ -1291,7 +1303,11 @@ int bse_create_batched(int count, const int64_t* N, const void* const* A, const 
       }
   }
   if (rc == BSE_OK && jobs.size() > 2147483647ull) rc = BSE_EINVAL;
-  if (rc == BSE_OK && h->mixed) h->hjobs = jobs;
+  if (rc == BSE_OK && h->mixed) {
+    h->hjobs = jobs;
+    rc = dalloc((void**)&h->prod_err, sizeof(int));
+    if (rc == BSE_OK && cudaMemsetAsync(h->prod_err, 0, sizeof(int), h->stream) != cudaSuccess) rc = BSE_ECUDA;
+  }
   if (rc == BSE_OK) {
     h->njobs = (int)jobs.size();
     rc = dalloc((void**)&h->djobs, sizeof(TileJob) * jobs.size());
@@ -1381,10 +1397,13 @@ int bse_apply_mixed(bse_handle* h, int op, double tile_tau, const void* X, void*
   io.y = q.pw;
   io.sB = op == BSE_OP_MPLUS ? 1.0 : -1.0;
   launch_product_mixed(h->dprobs, h->djobs_fine, h->njobs_fine, h->djobs_coarse, h->njobs_coarse, 1, h->maxnT,
-                       PM_GENERIC, &io, h->shape, h->stream);
+                       PM_GENERIC, &io, h->shape, h->prod_err, h->stream);
   CK(cudaMemcpyAsync(Y, q.pw, sizeof(double2) * (size_t)q.N, cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaGetLastError());
+  int perr = 0;
+  CK(cudaMemcpyAsync(&perr, h->prod_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (perr) return BSE_ETIMEOUT;
   h->stats.tiles_fine = h->njobs_fine;
   h->stats.tiles_coarse = h->njobs_coarse;
   return BSE_OK;
@@ -1436,6 +1455,7 @@ int bse_destroy(bse_handle* h) {
   }
   dfreet(h->djobs_fine);
   dfreet(h->djobs_coarse);
+  dfreet(h->prod_err);
   dfreet(h->dprobs);
   dfreet(h->dstate);
   dfreet(h->djobs);

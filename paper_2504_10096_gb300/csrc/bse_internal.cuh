@@ -121,6 +121,8 @@ struct Prob {
   // complex64 PH handles on the mixed path: per tile, an upper bound on every
   // |U|, |V| component (U, V = A +- B), indexed like the packed tiles
   const float* tmax;
+  void* xs;           // mixed PH path: the pre-split vector of a product, 2 x Npad x 32 B
+  float* xmax;        // ... and the max |hi part| of each 128-entry chunk [nT]
 };
 
 // Jobs of the tiled product: problem, tile row I, tile column J, tile index.
@@ -194,10 +196,12 @@ void launch_split_tiles(const double2* packed, int64_t nelem, float4* split, cud
 // "fine" tiles (k_prod_tiles_df2), fixed-point-grid accumulation with rounded U, V on
 // the "coarse" ones (k_prod_tiles_mx), then the FP64 reduction (k_product_df.cu)
 void launch_product_mixed(const Prob* dprobs, const TileJob* fine, int nfine, const TileJob* coarse, int ncoarse,
-                          int nprob, int maxnT, int mode, const GenericIO* io_host, ProdShape shape, cudaStream_t s);
+                          int nprob, int maxnT, int mode, const GenericIO* io_host, ProdShape shape, int* err,
+                          cudaStream_t s);
 int product_mx_occupancy();
 // per-tile bound max(|A_re| + |B_re|, |A_im| + |B_im|) of complex64 tiles (k_product_df.cu)
 void launch_tile_bound(const float2* A, const float2* B, int64_t ntiles, float* out, cudaStream_t s);
+// sums the float4 (hi, lo) partial-sum slots of the double-FP32 kernels in FP64 (k_product.cu)
 void launch_prod_reduce_d(const Prob* dprobs, int nprob, int maxnT, int mode, GenericIO io, cudaStream_t s);
 
 // bounded-wait self-test (k_adjoint_tc.cu): 0 on success, -1 on a CUDA error

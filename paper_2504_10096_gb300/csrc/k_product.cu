@@ -240,6 +240,39 @@ k_prod_reduce(const Prob* __restrict__ probs, int mode, GenericIO io) {
   }
 }
 
+// Same reduction for the double-FP32 kernels, whose slots hold (hi, lo) float
+// pairs {re_hi, re_lo, im_hi, im_lo}: each slot is widened to FP64 and the slots
+// are summed in FP64 in the fixed order above.
+__global__ void __launch_bounds__(REDUCE_GROUPS * TS)
+k_prod_reduce_dfc(const Prob* __restrict__ probs, int mode, GenericIO io) {
+  __shared__ double2 grp[REDUCE_GROUPS - 1][TS];
+  const Prob& p = probs[blockIdx.y];
+  const int I = blockIdx.x;
+  if (I >= p.nT) return;
+  const double2* x; double2* y; double sB;
+  if (!prod_operands<double2, double>(p, mode, io, x, y, sB)) return;
+  const int r = threadIdx.x & (TS - 1), g = threadIdx.x >> 7;
+  const float4* part = (const float4*)p.part + (int64_t)I * p.nT * TS;
+  double2 acc = make_double2(0.0, 0.0);
+  auto wide = [](float4 v) { return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w); };
+  int J = g;
+  for (; J + 3 * REDUCE_GROUPS < p.nT; J += 4 * REDUCE_GROUPS) {
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = part[(int64_t)(J + u * REDUCE_GROUPS) * TS + r];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc = cadd(acc, wide(v[u]));
+  }
+  for (; J < p.nT; J += REDUCE_GROUPS) acc = cadd(acc, wide(part[(int64_t)J * TS + r]));
+  if (g > 0) grp[g - 1][r] = acc;
+  __syncthreads();
+  if (g == 0) {
+#pragma unroll
+    for (int q = 0; q < REDUCE_GROUPS - 1; ++q) acc = cadd(acc, grp[q][r]);
+    y[(int64_t)I * TS + r] = acc;
+  }
+}
+
 // ---------------------------------------------------------------- wide blocks
 // Y[:, c0:c0+16] of block row I = sum_J Ablk(I,J) XA_J + sB Bblk(I,J) XB_J,
 // Ablk(I,J) = tile(I,J) for J >= I, tile(J,I)^H otherwise; Bblk uses ^T.
@@ -490,7 +523,7 @@ void launch_product(const Prob* dprobs, const TileJob* jobs, int njobs, int npro
 }
 
 void launch_prod_reduce_d(const Prob* dprobs, int nprob, int maxnT, int mode, GenericIO io, cudaStream_t s) {
-  k_prod_reduce<double2, double><<<dim3(maxnT, nprob), REDUCE_GROUPS * TS, 0, s>>>(dprobs, mode, io);
+  k_prod_reduce_dfc<<<dim3(maxnT, nprob), REDUCE_GROUPS * TS, 0, s>>>(dprobs, mode, io);
 }
 
 template void launch_product<double2, double>(const Prob*, const TileJob*, int, int, int, int, int,

@@ -85,9 +85,9 @@ __device__ __forceinline__ DFC dfc_shfl(DFC v, int m) {
   return v;
 }
 
-__device__ __forceinline__ double2 dfc_to_d(const DFC& v) {
-  return make_double2((double)v.rh + (double)v.rl, (double)v.ih + (double)v.il);
-}
+// partial-sum slots of the double-FP32 kernels hold the (hi, lo) pairs as
+// float4 {re_hi, re_lo, im_hi, im_lo}; k_prod_reduce_dfc adds them in FP64
+__device__ __forceinline__ float4 dfc_pack(const DFC& v) { return make_float4(v.rh, v.rl, v.ih, v.il); }
 
 __device__ __forceinline__ float4 split_d(double2 a) {
   const float rh = __double2float_rn(a.x), ih = __double2float_rn(a.y);
@@ -144,8 +144,8 @@ __device__ __forceinline__ void df_tile_reduce(DFC (&racc)[8], DFC (&cacc)[8], D
     racc[0] = dfc_add(k, dfc_shfl(s, 2));
     racc[0] = dfc_add(racc[0], dfc_shfl(racc[0], 1));
     if ((tx & 1) == 0) {
-      double2* part = (double2*)p.part;
-      part[((int64_t)jb.I * p.nT + jb.J) * TS + ty + 16 * ((tx >> 1) & 7)] = dfc_to_d(racc[0]);
+      float4* part = (float4*)p.part;
+      part[((int64_t)jb.I * p.nT + jb.J) * TS + ty + 16 * ((tx >> 1) & 7)] = dfc_pack(racc[0]);
     }
   }
   if (!diag) {
@@ -162,8 +162,8 @@ __device__ __forceinline__ void df_tile_reduce(DFC (&racc)[8], DFC (&cacc)[8], D
       DFC s = red[0][tid];
 #pragma unroll
       for (int w = 1; w < 8; ++w) s = dfc_add(s, red[w][tid]);
-      double2* part = (double2*)p.part;
-      part[((int64_t)jb.J * p.nT + jb.I) * TS + tid] = dfc_to_d(s);
+      float4* part = (float4*)p.part;
+      part[((int64_t)jb.J * p.nT + jb.I) * TS + tid] = dfc_pack(s);
     }
   }
 }
@@ -491,7 +491,7 @@ k_prod_tiles_df2(const Prob* __restrict__ probs, const TileJob* __restrict__ job
 // (2) every product of U with the double-FP32 vector x = xh + xl is
 //     accumulated on a fixed-point grid: each chain starts at sigma = 1.5 2^e
 //     with 2^(e-1) above the largest partial sum the chain can reach (from the
-//     tile's bound on |U| and the staged chunk's max |xh|), so the chain value
+//     tile's bound on |U| and the chunk's max |xh|), so the chain value
 //     H = sigma + S stays in [2^e, 2^(e+1)) and every
 //         t = fma(U, xh, H)   (H + U xh rounded to the grid 2^(e-23))
 //         d = t - H           (exact: both on the grid, |d| < 2^e)
@@ -504,9 +504,16 @@ k_prod_tiles_df2(const Prob* __restrict__ probs, const TileJob* __restrict__ job
 //     TwoSum in k_prod_tiles_df2; the chain error is about 2^-35 of
 //     max|U| max|xh| (the tail's own FP32 rounding), so tiles with big
 //     entries stay on k_prod_tiles_df2.
-// Row and column chain results leave as normalised double-FP32 pairs and go
-// through the same cross-lane reduction and FP64 partial-sum slots as the
-// other double-FP32 kernels.
+//
+// Data movement: one CTA of 512 threads per SM walks its tile jobs; the tile
+// rows stream through a three-stage shared-memory pipeline of 32-row slabs of
+// A and B (64 KiB a stage) filled by bulk asynchronous copies (cp.async.bulk,
+// completion counted on an mbarrier), so ~190 KiB per SM are in flight while
+// the registers hold only accumulators.  The vector enters pre-split
+// (k_mx_stage_x, once per product: hi/lo pairs in both pairings, and the max
+// |xh| of every 128-entry chunk) and its two chunks ride along with a tile's
+// first slab.  Every wait is bounded: on expiry the CTA stops, waits (bounded)
+// for its copies in flight, and raises the caller's error flag.
 __device__ __forceinline__ float grid_sigma(float m, int headroom) {
   // 1.5 2^e with e = exponent(m) + headroom; m >= 0 (0 for an all-zero operand)
   int e = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127 + headroom;
@@ -514,7 +521,7 @@ __device__ __forceinline__ float grid_sigma(float m, int headroom) {
   return __uint_as_float(((unsigned)(e + 127) << 23) | 0x400000u);
 }
 
-struct XMix { f2 h1, l1, h2, l2; };   // hi / lo of the two operand pairings of one vector entry
+struct alignas(16) XMix { f2 h1, l1, h2, l2; };   // hi / lo of the two operand pairings of one vector entry
 
 __device__ __forceinline__ XMix xmix(double2 v, bool row) {
   const float4 s = split_d(v);           // {re_hi, im_hi, re_lo, im_lo}
@@ -547,86 +554,176 @@ __device__ __forceinline__ void two_sum1(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
 }
 
-__global__ void __launch_bounds__(PROD_THREADS, 2)
+// x of every active problem -> xs[0][r] (column pairing), xs[1][r] (row pairing)
+// and xmax[I] = max |xh| over chunk I; grid (maxnT, nprob), TS threads
+__global__ void __launch_bounds__(TS)
+k_mx_stage_x(const Prob* __restrict__ probs, int mode, GenericIO io) {
+  __shared__ float sm[TS / 32];
+  const Prob& p = probs[blockIdx.y];
+  const int I = blockIdx.x;
+  if (I >= p.nT) return;
+  const double2* x;
+  double sB;
+  if (!df_operands(p, mode, io, x, sB)) return;
+  const int64_t r = (int64_t)I * TS + threadIdx.x;
+  const double2 v = x[r];
+  XMix* xs = (XMix*)p.xs;
+  const XMix c = xmix(v, false);
+  xs[r] = c;
+  xs[p.Npad + r] = xmix(v, true);
+  float a0, a1;
+  upk(c.h1, a0, a1);
+  float m = fmaxf(fabsf(a0), fabsf(a1));
+#pragma unroll
+  for (int k = 16; k >= 1; k >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, k));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = sm[0];
+#pragma unroll
+    for (int w = 1; w < TS / 32; ++w) t = fmaxf(t, sm[w]);
+    p.xmax[I] = t;
+  }
+}
+
+constexpr int MX_THREADS = 512;                       // 16 column lanes x 32 row lanes
+constexpr int MX_ROWS = 32;                           // rows of a slab
+constexpr int MX_SLABS = TS / MX_ROWS;                // slabs per tile
+constexpr int MX_NST = 3;                             // pipeline stages
+constexpr uint32_t MX_HALF = MX_ROWS * TS * 8;        // one matrix's slab: 32 KiB
+constexpr uint32_t MX_STAGE = 2 * MX_HALF;            // A and B: 64 KiB
+constexpr uint32_t MX_XBYTES = TS * sizeof(XMix);     // one staged vector chunk: 4 KiB
+constexpr uint32_t MX_XOFF = MX_NST * MX_STAGE;       // two x buffers of (column, row) chunks
+constexpr uint32_t MX_REDOFF = MX_XOFF + 2 * 2 * MX_XBYTES;
+constexpr uint32_t MX_SMEM = MX_REDOFF + 8 * TS * sizeof(DFC);   // + column-reduction buffer: 224 KiB
+constexpr long long MX_SPIN = 1ll << 26;              // polls of a bounded wait
+
+__device__ __forceinline__ uint32_t mx_s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mx_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mx_wait(uint32_t bar, uint32_t parity) {
+  for (long long i = 0; i < MX_SPIN; ++i)
+    if (mx_try(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void mx_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(MX_THREADS, 1)
 k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs, int njobs, int mode,
-                GenericIO io, int strided) {
-  __shared__ XMix xc[TS], xr[TS];
-  __shared__ DFC rpark[8][PROD_THREADS];
-  __shared__ float smax[8];
-  DFC(*red)[TS] = reinterpret_cast<DFC(*)[TS]>(&rpark[0][0]);
+                GenericIO io, int strided, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smx[];
+  __shared__ uint64_t full[MX_NST];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int per = strided ? 1 : (njobs + gridDim.x - 1) / gridDim.x;
   const int t0 = strided ? blockIdx.x : blockIdx.x * per;
   const int t1 = strided ? njobs : min(njobs, t0 + per);
   const int dt = strided ? gridDim.x : 1;
+  if (tid == 0) {
+    for (int s = 0; s < MX_NST; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mx_s32(&full[s])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto active = [&](int t) {
+    const double2* xx;
+    double sb;
+    return df_operands(probs[jobs[t].prob], mode, io, xx, sb);
+  };
+  // producer cursor (thread 0): the next (job, slab) to copy, and the active-tile ordinal
+  int pt = t0, pa = 0, ptile = 0;
+  long long issued = 0;
+  auto produce = [&](long long consumed) {
+    while (issued < consumed + MX_NST) {
+      if (pa == 0) {
+        while (pt < t1 && !active(pt)) pt += dt;
+        if (pt >= t1) return;
+      }
+      const TileJob jb = jobs[pt];
+      const Prob& p = probs[jb.prob];
+      const int s = (int)(issued % MX_NST);
+      const uint32_t bar = mx_s32(&full[s]);
+      const uint32_t st = mx_s32(smx) + (uint32_t)s * MX_STAGE;
+      const size_t off = ((size_t)jb.t * TS + (size_t)pa * MX_ROWS) * TS;
+      const uint32_t bytes = MX_STAGE + (pa == 0 ? 2 * MX_XBYTES : 0u);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+      mx_copy(st, (const float2*)p.A + off, MX_HALF, bar);
+      mx_copy(st + MX_HALF, (const float2*)p.B + off, MX_HALF, bar);
+      if (pa == 0) {   // the tile's two vector chunks, into the x buffer of its parity
+        const uint32_t xb = mx_s32(smx) + MX_XOFF + (uint32_t)(ptile & 1) * 2 * MX_XBYTES;
+        const XMix* xs = (const XMix*)p.xs;
+        mx_copy(xb, xs + (int64_t)jb.J * TS, MX_XBYTES, bar);
+        mx_copy(xb + MX_XBYTES, xs + p.Npad + (int64_t)jb.I * TS, MX_XBYTES, bar);
+      }
+      ++issued;
+      if (++pa == MX_SLABS) {
+        pa = 0;
+        pt += dt;
+        ++ptile;
+      }
+    }
+  };
+  if (tid == 0) produce(0);
+  DFC(*red)[TS] = reinterpret_cast<DFC(*)[TS]>(smx + MX_REDOFF);
   const f2 zero = pk(0.f, 0.f);
-  for (int t = t0; t < t1; t += dt) {
+  long long consumed = 0;
+  int ctile = 0;
+  bool ok = true;
+  for (int t = t0; t < t1 && ok; t += dt) {
     const TileJob jb = jobs[t];
     const Prob& p = probs[jb.prob];
     const double2* x;
     double sB;
     if (!df_operands(p, mode, io, x, sB)) continue;   // uniform per CTA
     const bool diag = jb.I == jb.J;
-    __syncthreads();
-    float mx;
-    {
-      const int r = tid & (TS - 1);
-      const double2 v = x[(int64_t)(tid < TS ? jb.J : jb.I) * TS + r];
-      const XMix o = xmix(v, tid >= TS);
-      if (tid < TS) xc[r] = o;
-      else xr[r] = o;
-      float a0, a1;
-      upk(o.h1, a0, a1);
-      mx = fmaxf(fabsf(a0), fabsf(a1));
-#pragma unroll
-      for (int m = 16; m >= 1; m >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, m));
-      if ((tid & 31) == 0) smax[tid >> 5] = mx;
-    }
-    __syncthreads();
-    mx = smax[0];
-#pragma unroll
-    for (int w = 1; w < 8; ++w) mx = fmaxf(mx, smax[w]);
-    // bound on every |U xh| of this tile; row chains sum 8 such products per lane,
-    // column chains 16; one more bit absorbs the roundings of U, of the bound and
-    // of the grid itself
-    const float m = p.tmax[jb.t] * mx;
-    const float sgr = grid_sigma(m, 6), sgc = grid_sigma(m, 7);
-    const f2 sr2 = pk(sgr, sgr), sc2 = pk(sgc, sgc);
-    const float2* At = (const float2*)p.A + (int64_t)jb.t * (TS * TS);
-    const float2* Bt = (const float2*)p.B + (int64_t)jb.t * (TS * TS);
-    const float sg = sB > 0.0 ? 1.f : -1.f;
-    const f2 spm = pk(sg, -sg);
+    const XMix* xc = reinterpret_cast<const XMix*>(smx + MX_XOFF + (ctile & 1) * 2 * MX_XBYTES);
+    const XMix* xr = xc + TS;
+    // bound m on every |U xh| of this tile (m < 2^(k+1), k its exponent); row chains sum 8
+    // such products per lane, column chains 8 (4 rows x 2), so |S| < 2^(k+4) (1 + 3 u); the
+    // grid 2^e with e = k + 6 keeps |S| below 2^(e-1) with a factor 2 to spare
+    const float m = p.tmax[jb.t] * fmaxf(p.xmax[jb.I], p.xmax[jb.J]);
+    const float sg = grid_sigma(m, 6);
+    const f2 sg2 = pk(sg, sg);
+    const float sgn = sB > 0.0 ? 1.f : -1.f;
+    const f2 spm = pk(sgn, -sgn);
     f2 cH[8], cL[8];
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
-      cH[b] = sc2;
+      cH[b] = sg2;
       cL[b] = zero;
     }
-    float2 av[8], bv[8];
+    DFC racc[MX_SLABS];
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      av[b] = __ldg(At + ty * TS + tx + 16 * b);
-      bv[b] = __ldg(Bt + ty * TS + tx + 16 * b);
-    }
-#pragma unroll 1
-    for (int a = 0; a < 8; ++a) {
-      const int r = ty + 16 * a;
-      float2 an[8], bn[8];
-      if (a < 7) {                          // the next row's elements are in flight meanwhile
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          an[b] = __ldg(At + (r + 16) * TS + tx + 16 * b);
-          bn[b] = __ldg(Bt + (r + 16) * TS + tx + 16 * b);
-        }
-      }
-      const XMix y = xr[r];
-      f2 H1 = sr2, L1 = zero, H2 = sr2, L2 = zero;
+    for (int a = 0; a < MX_SLABS; ++a) {
+      const int s = (int)(consumed % MX_NST);
+      const bool got = mx_wait(mx_s32(&full[s]), (uint32_t)((consumed / MX_NST) & 1));
+      if (__syncthreads_or(got ? 0 : 1)) { ok = false; break; }
+      const float2* As = reinterpret_cast<const float2*>(smx + (size_t)s * MX_STAGE) + ty * TS + tx;
+      const float2* Bs = As + MX_ROWS * TS;
+      const XMix y = xr[ty + MX_ROWS * a];
+      f2 H1 = sg2, L1 = zero, H2 = sg2, L2 = zero;
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
+        const float2 av = As[16 * b], bv = Bs[16 * b];
         const XMix xv = xc[tx + 16 * b];
         // (U_re, V_re) and (U_im, V_im), rounded
-        const f2 uvr = fma2(pk(bv[b].x, bv[b].x), spm, pk(av[b].x, av[b].x));
-        const f2 uvi = fma2(pk(bv[b].y, bv[b].y), spm, pk(av[b].y, av[b].y));
+        const f2 uvr = fma2(pk(bv.x, bv.x), spm, pk(av.x, av.x));
+        const f2 uvi = fma2(pk(bv.y, bv.y), spm, pk(av.y, av.y));
         gacc(H1, L1, uvr, xv.h1, xv.l1);
         gacc(H2, L2, uvi, xv.h2, xv.l2);
         if (!diag) {
@@ -636,35 +733,92 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
       }
       // y_re = lane 0 of chain 1 + lane 1 of chain 2, y_im = lane 1 of 1 + lane 0 of 2;
       // the grid parts add exactly, then (grid, tail) is normalised
-      const f2 S1 = sub2(H1, sr2), S2 = sub2(H2, sr2);
       float s1a, s1b, s2a, s2b, l1a, l1b, l2a, l2b;
-      upk(S1, s1a, s1b);
-      upk(S2, s2a, s2b);
+      upk(sub2(H1, sg2), s1a, s1b);
+      upk(sub2(H2, sg2), s2a, s2b);
       upk(L1, l1a, l1b);
       upk(L2, l2a, l2b);
-      DFC ra;
-      two_sum1(__fadd_rn(s1a, s2b), __fadd_rn(l1a, l2b), ra.rh, ra.rl);
-      two_sum1(__fadd_rn(s1b, s2a), __fadd_rn(l1b, l2a), ra.ih, ra.il);
-      rpark[a][tid] = ra;
+      two_sum1(__fadd_rn(s1a, s2b), __fadd_rn(l1a, l2b), racc[a].rh, racc[a].rl);
+      two_sum1(__fadd_rn(s1b, s2a), __fadd_rn(l1b, l2a), racc[a].ih, racc[a].il);
+      __syncthreads();                 // every thread is done with stage s
+      ++consumed;
+      if (tid == 0) produce(consumed);
+    }
+    if (!ok) break;
+    ++ctile;
+    // ---- row sums: reduce-scatter of the 4 rows over the 16 column lanes, then the
+    // remaining pairs; lanes tx % 4 == 0 write row ty + 32 ((tx >> 3) * 2 + ((tx >> 2) & 1))
+    {
+      const bool u8 = tx & 8;
 #pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        av[b] = an[b];
-        bv[b] = bn[b];
+      for (int q = 0; q < 2; ++q) {
+        const DFC snd = u8 ? racc[q] : racc[q + 2], kp = u8 ? racc[q + 2] : racc[q];
+        racc[q] = dfc_add(kp, dfc_shfl(snd, 8));
+      }
+      const bool u4 = tx & 4;
+      {
+        const DFC snd = u4 ? racc[0] : racc[1], kp = u4 ? racc[1] : racc[0];
+        racc[0] = dfc_add(kp, dfc_shfl(snd, 4));
+      }
+      racc[0] = dfc_add(racc[0], dfc_shfl(racc[0], 2));
+      racc[0] = dfc_add(racc[0], dfc_shfl(racc[0], 1));
+      if ((tx & 3) == 0) {
+        const int a = (u8 ? 2 : 0) + (u4 ? 1 : 0);
+        float4* part = (float4*)p.part;
+        part[((int64_t)jb.I * p.nT + jb.J) * TS + ty + MX_ROWS * a] = dfc_pack(racc[0]);
       }
     }
-    DFC racc[8], cacc[8];
+    if (!diag) {
+      // ---- column sums over the 32 row lanes: the two of a warp (xor 16), then 16 warps
+      // in two rounds through an 8 x TS buffer
+      const int lane = tid & 31, warp = tid >> 5;
+      DFC cacc[8];
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      float hr, hi, lr, li;
-      upk(sub2(cH[b], sc2), hr, hi);
-      upk(cL[b], lr, li);
-      two_sum1(hr, lr, cacc[b].rh, cacc[b].rl);
-      two_sum1(hi, li, cacc[b].ih, cacc[b].il);
+      for (int b = 0; b < 8; ++b) {
+        float hr, hi, lr, li;
+        upk(sub2(cH[b], sg2), hr, hi);
+        upk(cL[b], lr, li);
+        two_sum1(hr, lr, cacc[b].rh, cacc[b].rl);
+        two_sum1(hi, li, cacc[b].ih, cacc[b].il);
+      }
+      const bool up = lane & 16;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const DFC snd = up ? cacc[q] : cacc[q + 4], kp = up ? cacc[q + 4] : cacc[q];
+        cacc[q] = dfc_add(kp, dfc_shfl(snd, 16));
+      }
+      // lane holds columns tx + 16 (q + 4 up), q < 4
+      if (warp >= 8) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) red[warp - 8][tx + 16 * (q + (up ? 4 : 0))] = cacc[q];
+      }
+      __syncthreads();
+      if (warp < 8) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = tx + 16 * (q + (up ? 4 : 0));
+          red[warp][c] = dfc_add(cacc[q], red[warp][c]);
+        }
+      }
+      __syncthreads();
+      if (tid < TS) {
+        DFC sum = red[0][tid];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) sum = dfc_add(sum, red[w][tid]);
+        float4* part = (float4*)p.part;
+        part[((int64_t)jb.J * p.nT + jb.I) * TS + tid] = dfc_pack(sum);
+      }
+      __syncthreads();                 // red is free for the next tile
     }
-#pragma unroll
-    for (int a = 0; a < 8; ++a) racc[a] = rpark[a][tid];
-    __syncthreads();   // rpark is reused below as the column-reduction buffer
-    df_tile_reduce(racc, cacc, red, diag, p, jb);
+  }
+  if (!ok) {
+    if (tid == 0) {
+      atomicExch(err, 1);
+      // nothing may land in shared memory after the CTA exits: wait (bounded) for the copies
+      for (long long g = consumed; g < issued; ++g)
+        mx_wait(mx_s32(&full[g % MX_NST]), (uint32_t)((g / MX_NST) & 1));
+    }
+    __syncthreads();
   }
 }
 
@@ -749,18 +903,11 @@ void launch_product_df(const Prob* dprobs, const TileJob* jobs, int njobs, int n
   launch_prod_reduce_d(dprobs, nprob, maxnT, mode, io, s);
 }
 
-int product_mx_occupancy() {
-  static int occ = 0;
-  if (!occ) {
-    int o = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_prod_tiles_mx, PROD_THREADS, 0);
-    occ = o > 0 ? o : 1;
-  }
-  return occ;
-}
+int product_mx_occupancy() { return 1; }   // one 512-thread CTA with 224 KiB of shared memory per SM
 
 void launch_product_mixed(const Prob* dprobs, const TileJob* fine, int nfine, const TileJob* coarse, int ncoarse,
-                          int nprob, int maxnT, int mode, const GenericIO* io_host, ProdShape shape, cudaStream_t s) {
+                          int nprob, int maxnT, int mode, const GenericIO* io_host, ProdShape shape, int* err,
+                          cudaStream_t s) {
   GenericIO io{};
   if (io_host) io = *io_host;
   if (nfine > 0) {
@@ -770,9 +917,16 @@ void launch_product_mixed(const Prob* dprobs, const TileJob* fine, int nfine, co
         dprobs, fine, nfine, mode, io, 1);
   }
   if (ncoarse > 0) {
-    count_launch();
-    k_prod_tiles_mx<<<product_grid(product_mx_occupancy(), shape, ncoarse), PROD_THREADS, 0, s>>>(
-        dprobs, coarse, ncoarse, mode, io, shape.strided);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_prod_tiles_mx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MX_SMEM);
+      attr = true;
+    }
+    count_launch(2);
+    k_mx_stage_x<<<dim3(maxnT, nprob), TS, 0, s>>>(dprobs, mode, io);
+    const ProdShape ms{1, shape.strided};
+    k_prod_tiles_mx<<<product_grid(1, ms, ncoarse), MX_THREADS, MX_SMEM, s>>>(dprobs, coarse, ncoarse, mode, io,
+                                                                             shape.strided, err);
   }
   count_launch();
   launch_prod_reduce_d(dprobs, nprob, maxnT, mode, io, s);

@@ -267,6 +267,27 @@ int bse_backward_ex(bse_handle* h, const double* dL_dlambda, int where, void* dA
 int bse_apply(bse_handle* h, int op, int k, const void* X, void* Y);
 
 /*
+ * bse_solve_dense -- the nev lowest positive eigenpairs of a single-problem
+ * pseudo-Hermitian handle by dense, structure-preserving diagonalisation
+ * (Sec. 2.1.1, Eqs. 4-6: M_r of Eq. 5, its Cholesky factor L, the real
+ * skew-symmetric W = L^T J L, Householder reduction of W to skew-tridiagonal
+ * form, bisection and inverse iteration on the equivalent real symmetric
+ * tridiagonal matrix, back-transformation and z = Q L^{-T} q).  The direct
+ * method of the paper for the regime where a large share of the spectrum is
+ * wanted; O(N^3) work, FP64 throughout whatever the storage dtype.
+ *   tol        a pair counts in *nconv_out if its FP64 relative residual is
+ *              <= tol (as in bse_solve; e.g. 1e-10)
+ *   eval_out   host, nev doubles (FP64 Rayleigh quotients, ascending)
+ *   evec_out   device or NULL: 2N x nev, column-major, handle dtype,
+ *              Omega-normalised
+ * Allocates about 2 (2N)^2 doubles of scratch for the call.  BSE_ENOTPD if
+ * M_r is not positive definite, BSE_ENOCONV if fewer than nev pairs pass
+ * the residual test, BSE_EINVAL for TDA or batched handles.  The
+ * eigenvectors stay in the handle for bse_backward.
+ */
+int bse_solve_dense(bse_handle* h, int nev, double tol, double* eval_out, void* evec_out, int* nconv_out);
+
+/*
  * bse_apply_mixed -- the mixed path's Lanczos product on one vector:
  *   y = A x + B conj(x)   (op BSE_OP_MPLUS)
  *   y = A x - B conj(x)   (op BSE_OP_MMINUS)

@@ -28,7 +28,7 @@ BSE_OP_A, BSE_OP_MPLUS, BSE_OP_MMINUS, BSE_OP_H = 0, 1, 2, 3
 EXPORTED = ["bse_strerror", "bse_create", "bse_create_batched", "bse_solve", "bse_solve_ex",
             "bse_solve_batched", "bse_backward", "bse_apply", "bse_get_stats", "bse_destroy",
             "bse_apply_noalloc", "bse_backward_ex", "bse_haydock", "bse_selftest_bounded_wait",
-            "bse_get_residuals", "bse_apply_mixed", "bse_measure_fp64_peak"]
+            "bse_get_residuals", "bse_apply_mixed", "bse_measure_fp64_peak", "bse_solve_dense"]
 BSE_IMPL_AUTO, BSE_IMPL_CUDA_CORES, BSE_IMPL_TENSOR_CORES = 0, 1, 2
 BSE_NOALLOC_MAX_N = 4096
 
@@ -85,6 +85,7 @@ def load_library(path: str | None = None):
     lib.bse_get_stats.argtypes = [H, ctypes.POINTER(bse_stats)]
     lib.bse_get_residuals.argtypes = [H, c_int, ctypes.POINTER(c_dbl), c_int]
     lib.bse_apply_mixed.argtypes = [H, c_int, c_dbl, c_vp, c_vp]
+    lib.bse_solve_dense.argtypes = [H, c_int, c_dbl, ctypes.POINTER(c_dbl), c_vp, ctypes.POINTER(c_int)]
     lib.bse_measure_fp64_peak.argtypes = [c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl)]
     lib.bse_destroy.argtypes = [H]
     lib.bse_apply_noalloc.argtypes = [c_i64, c_vp, c_vp, c_int, c_int, c_vp, c_vp, c_vp]
@@ -185,6 +186,14 @@ def bse_selftest_bounded_wait(arrive):
 
 def bse_apply(h, op, k, X_ptr, Y_ptr):
     return load_library().bse_apply(h, op, k, X_ptr, Y_ptr)
+
+
+def bse_solve_dense(h, nev, tol, evec_ptr=None):
+    """Dense structure-preserving diagonalisation (see bse.h): (status, eigenvalues, nconv)."""
+    ev = (ctypes.c_double * nev)()
+    nconv = ctypes.c_int(0)
+    rc = load_library().bse_solve_dense(h, nev, float(tol), ev, evec_ptr, ctypes.byref(nconv))
+    return rc, np.array(ev[:], dtype=np.float64), nconv.value
 
 
 def bse_apply_mixed(h, op, tile_tau, x_ptr, y_ptr):
@@ -316,6 +325,17 @@ class Solver:
         self.status = rc
         vecs = ev.T if ev is not None else None   # (rows, nev) column-major view
         return vals, vecs, nconv
+
+    def solve_dense(self, nev, tol=1e-10, vectors=True, check=True):
+        """Dense structure-preserving diagonalisation (bse_solve_dense), PH handles only."""
+        torch = _torch()
+        ev = torch.empty((nev, 2 * self.N), dtype=self.cdtype, device=self.device) if vectors else None
+        rc, vals, nconv = bse_solve_dense(self.h, nev, tol, ev.data_ptr() if ev is not None else None)
+        if check:
+            _check(rc, "bse_solve_dense")
+        self.nev = nev
+        self.status = rc
+        return vals, (ev.T if ev is not None else None), nconv
 
     def apply(self, op, X):
         """Y = op(X) for a device block X (rows x k, any layout; k columns)."""

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbse.so")
 SOURCES = ["k_product.cu", "k_product_df.cu", "k_krylov.cu", "k_ritz.cu", "k_post.cu", "bse_api.cu",
-           "k_noalloc.cu", "k_adjoint_tc.cu", "k_haydock.cu", "k_peak.cu"]
+           "k_noalloc.cu", "k_adjoint_tc.cu", "k_haydock.cu", "k_peak.cu", "k_dense.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

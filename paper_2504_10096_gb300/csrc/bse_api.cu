@@ -496,24 +496,40 @@ struct Driver {
     return BSE_OK;
   }
 
-  // recover eigenvectors, FP64 residuals and Rayleigh quotients of problem i;
-  // a pair counts as converged only if its FP64 relative residual is <= tol
-  int finalize(int i, int nev, double tol) {
+  // result buffers of problem i for k pairs
+  int alloc_results(int i, int k) {
     ProbHost& q = h->p[i];
-    const KState& s = h->hstate[i];
     free_results(q);
-    const int k = std::min(s.k, nev);
     q.nconv = k;
     q.eval.assign(k, 0.0);
     q.res.assign(k, 0.0);
     if (k == 0) return BSE_OK;
-    const int64_t Npad = q.Npad;
-    const int64_t ldz = h->ph ? 2 * Npad : Npad;
+    const int64_t ldz = h->ph ? 2 * q.Npad : q.Npad;
     int rc = dalloc((void**)&q.Z, sizeof(double2) * (size_t)ldz * k);
     if (rc) return rc;
     rc = dalloc((void**)&q.perm, sizeof(int) * k);
     if (rc) return rc;
     q.zcols = k;
+    return BSE_OK;
+  }
+
+  // recover eigenvectors, FP64 residuals and Rayleigh quotients of problem i;
+  // a pair counts as converged only if its FP64 relative residual is <= tol
+  int finalize(int i, int nev, double tol) {
+    const KState& s = h->hstate[i];
+    const int k = std::min(s.k, nev);
+    int rc = alloc_results(i, k);
+    if (rc || k == 0) return rc;
+    return finish(i, k, tol, true);
+  }
+
+  // Omega- (or 2-) normalise the k columns of Z (recovered from the Krylov basis first when
+  // `recover`), FP64 products H z, Rayleigh quotients, residuals, output order
+  int finish(int i, int k, double tol, bool recover) {
+    ProbHost& q = h->p[i];
+    const int64_t Npad = q.Npad;
+    const int64_t ldz = h->ph ? 2 * Npad : Npad;
+    int rc;
     const int nrb = nrb_of(Npad);
     const int kc = h->ph ? 2 * k : k;
     // scratch: XA, XB, U (Npad x kc FP64 complex), part4 (k x nrb double4), rho, z2, res
@@ -533,7 +549,7 @@ struct Driver {
     double* rho = (double*)(part4 + (size_t)k * nrb);
     double* z2 = rho + k;
     double* res = z2 + k;
-    launch_recover<ST>(h->dprobs, i, h->ph, Npad, q.N, k, q.Z, (int)ldz, h->stream);
+    if (recover) launch_recover<ST>(h->dprobs, i, h->ph, Npad, q.N, k, q.Z, (int)ldz, h->stream);
     launch_colnormalize(q.Z, ldz, Npad, k, h->ph, (double*)part4, nrb, h->stream);
     // FP64 products with the stored tiles (complex64 or complex128)
     const void* xa = h->ph ? (const void*)XA : (const void*)q.Z;
@@ -1376,6 +1392,67 @@ int bse_apply(bse_handle* h, int op, int k, const void* X, void* Y) {
   if (op < BSE_OP_A || op > BSE_OP_H) return BSE_EINVAL;
   if (is_c64(h->dtype)) return apply_impl<float2>(h, op, k, X, Y);
   return apply_impl<double2>(h, op, k, X, Y);
+}
+
+int bse_solve_dense(bse_handle* h, int nev, double tol, double* eval_out, void* evec_out, int* nconv_out) {
+  if (!h || h->count != 1 || !h->ph || !eval_out || !(tol > 0.0)) return BSE_EINVAL;
+  ProbHost& q = h->p[0];
+  if (nev < 1 || nev > q.N) return BSE_EINVAL;
+  int rc;
+  if (!q.w || q.ncv == 0) {      // partial-sum and vector buffers of the FP64 residual products
+    if ((rc = alloc_solve(h, std::min<int64_t>(q.N, 8) > 1 ? (int)std::min<int64_t>(q.N, 8) : 1))) return rc;
+  }
+  if ((rc = upload_probs(h))) return rc;
+  const size_t nd = dense_scratch_doubles(q.N, nev);
+  void* work = nullptr;
+  if ((rc = dalloc(&work, sizeof(double) * nd))) return rc;
+  struct Free { void* b; ~Free() { cudaFree(b); } } guard{work};
+  if (!h->adj_err && (rc = dalloc((void**)&h->adj_err, sizeof(int)))) return rc;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, h->stream);
+  const long long launches0 = launch_counter();
+  h->solved = false;
+  h->nev = nev;
+  int status = BSE_OK;
+  if (h->vs == sizeof(float2)) {
+    Driver<float2> drv(h);
+    if ((rc = drv.alloc_results(0, nev))) return rc;
+    const int r = dense_shao(h->dprobs, q.N, q.Npad, h->tiles64, !h->tiles64, nev, (double*)work, h->adj_err, q.Z,
+                             nullptr, h->stream);
+    if (r < 0) return BSE_ECUDA;
+    if (r > 0) status = BSE_ENOTPD;
+    if ((rc = drv.finish(0, nev, tol, false))) return rc;
+    if (evec_out && (rc = drv.store(0, evec_out))) return rc;
+  } else {
+    Driver<double2> drv(h);
+    if ((rc = drv.alloc_results(0, nev))) return rc;
+    const int r = dense_shao(h->dprobs, q.N, q.Npad, h->tiles64, !h->tiles64, nev, (double*)work, h->adj_err, q.Z,
+                             nullptr, h->stream);
+    if (r < 0) return BSE_ECUDA;
+    if (r > 0) status = BSE_ENOTPD;
+    if ((rc = drv.finish(0, nev, tol, false))) return rc;
+    if (evec_out && (rc = drv.store(0, evec_out))) return rc;
+  }
+  cudaEventRecord(e1, h->stream);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int c = 0; c < nev; ++c) eval_out[c] = c < (int)q.eval.size() ? q.eval[c] : NAN;
+  if (nconv_out) *nconv_out = q.nconv;
+  double maxres = 0.0;
+  for (double r : q.res) maxres = std::max(maxres, r);
+  h->stats = bse_stats{};
+  h->stats.nconv = q.nconv;
+  h->stats.max_residual = maxres;
+  h->stats.ms_total = ms;
+  h->stats.launches = launch_counter() - launches0;
+  h->solved = true;
+  if (status == BSE_OK && q.nconv < nev) status = BSE_ENOCONV;
+  return status;
 }
 
 int bse_apply_mixed(bse_handle* h, int op, double tile_tau, const void* X, void* Y) {

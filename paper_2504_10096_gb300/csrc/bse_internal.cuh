@@ -237,6 +237,13 @@ int launch_adjoint_tc(const double2* Z, int64_t ldz, int64_t Npad, int64_t N, in
                       const int2* tiles128, int64_t ntiles, float* panels, int* derr, float2* dA, float2* dB,
                       cudaStream_t s);
 
+// dense structure-preserving diagonalisation (k_dense.cu): the nev lowest positive omega of
+// problem 0 of a PH handle and their right eigenvectors in Z (ld 2 Npad); returns 0, 1 (M_r not
+// positive definite) or -1 (CUDA error); `work` holds dense_scratch_doubles(N, nev) doubles
+size_t dense_scratch_doubles(int64_t N, int nev);
+int dense_shao(const Prob* dprobs, int64_t N, int64_t Npad, bool tiles64, bool pq, int nev, double* work,
+               int* dflag, double2* Z, double* lam_out, cudaStream_t s);
+
 // Krylov kernels (k_krylov.cu)
 template <typename ST>
 void launch_step_cgs(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t maxNpad,

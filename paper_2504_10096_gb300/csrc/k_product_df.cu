@@ -521,23 +521,6 @@ __device__ __forceinline__ float grid_sigma(float m, int headroom) {
   return __uint_as_float(((unsigned)(e + 127) << 23) | 0x400000u);
 }
 
-struct alignas(16) XMix { f2 h1, l1, h2, l2; };   // hi / lo of the two operand pairings of one vector entry
-
-__device__ __forceinline__ XMix xmix(double2 v, bool row) {
-  const float4 s = split_d(v);           // {re_hi, im_hi, re_lo, im_lo}
-  XMix o;
-  o.h1 = pk(s.x, s.y);
-  o.l1 = pk(s.z, s.w);
-  if (!row) {                            // column block x_J: (re, -im)
-    o.h2 = pk(s.x, -s.y);
-    o.l2 = pk(s.z, -s.w);
-  } else {                               // row block x_I: (im, -re)
-    o.h2 = pk(s.y, -s.x);
-    o.l2 = pk(s.w, -s.z);
-  }
-  return o;
-}
-
 // (H, L) += u (xh + xl) on the grid of H (see above), lane-wise
 __device__ __forceinline__ void gacc(f2& H, f2& L, f2 u, f2 xh, f2 xl) {
   const f2 t = fma2(u, xh, H);
@@ -554,8 +537,9 @@ __device__ __forceinline__ void two_sum1(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
 }
 
-// x of every active problem -> xs[0][r] (column pairing), xs[1][r] (row pairing)
-// and xmax[I] = max |xh| over chunk I; grid (maxnT, nprob), TS threads
+// x of every active problem, split once per product into chunks of 128 entries,
+// each {hi[128], lo[128]} of float2 (re, im) pairs (2 KiB, so one bulk copy stages a
+// chunk), and xmax[I] = max |hi| over chunk I; grid (maxnT, nprob), TS threads
 __global__ void __launch_bounds__(TS)
 k_mx_stage_x(const Prob* __restrict__ probs, int mode, GenericIO io) {
   __shared__ float sm[TS / 32];
@@ -566,14 +550,11 @@ k_mx_stage_x(const Prob* __restrict__ probs, int mode, GenericIO io) {
   double sB;
   if (!df_operands(p, mode, io, x, sB)) return;
   const int64_t r = (int64_t)I * TS + threadIdx.x;
-  const double2 v = x[r];
-  XMix* xs = (XMix*)p.xs;
-  const XMix c = xmix(v, false);
-  xs[r] = c;
-  xs[p.Npad + r] = xmix(v, true);
-  float a0, a1;
-  upk(c.h1, a0, a1);
-  float m = fmaxf(fabsf(a0), fabsf(a1));
+  const float4 v = split_d(x[r]);          // {re_hi, im_hi, re_lo, im_lo}
+  float2* xs = (float2*)p.xs + (int64_t)I * 2 * TS;
+  xs[threadIdx.x] = make_float2(v.x, v.y);
+  xs[TS + threadIdx.x] = make_float2(v.z, v.w);
+  float m = fmaxf(fabsf(v.x), fabsf(v.y));
 #pragma unroll
   for (int k = 16; k >= 1; k >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, k));
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
@@ -587,15 +568,16 @@ k_mx_stage_x(const Prob* __restrict__ probs, int mode, GenericIO io) {
 }
 
 constexpr int MX_THREADS = 512;                       // 16 column lanes x 32 row lanes
+constexpr int MX_WARPS = MX_THREADS / 32;
 constexpr int MX_ROWS = 32;                           // rows of a slab
 constexpr int MX_SLABS = TS / MX_ROWS;                // slabs per tile
 constexpr int MX_NST = 3;                             // pipeline stages
 constexpr uint32_t MX_HALF = MX_ROWS * TS * 8;        // one matrix's slab: 32 KiB
 constexpr uint32_t MX_STAGE = 2 * MX_HALF;            // A and B: 64 KiB
-constexpr uint32_t MX_XBYTES = TS * sizeof(XMix);     // one staged vector chunk: 4 KiB
+constexpr uint32_t MX_XBYTES = 2 * TS * 8;            // one staged vector chunk (hi, lo): 2 KiB
 constexpr uint32_t MX_XOFF = MX_NST * MX_STAGE;       // two x buffers of (column, row) chunks
 constexpr uint32_t MX_REDOFF = MX_XOFF + 2 * 2 * MX_XBYTES;
-constexpr uint32_t MX_SMEM = MX_REDOFF + 8 * TS * sizeof(DFC);   // + column-reduction buffer: 224 KiB
+constexpr uint32_t MX_SMEM = MX_REDOFF + 8 * TS * sizeof(DFC);   // + column-reduction buffer
 constexpr long long MX_SPIN = 1ll << 26;              // polls of a bounded wait
 
 __device__ __forceinline__ uint32_t mx_s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -624,19 +606,30 @@ __device__ __forceinline__ void mx_copy(uint32_t dst, const void* src, uint32_t 
       : "memory");
 }
 
+__device__ __forceinline__ f2 f2lo(float4 v) { return pk(v.x, v.y); }
+__device__ __forceinline__ f2 f2hi(float4 v) { return pk(v.z, v.w); }
+
+// Thread (tx, ty) = (tid % 16, tid / 16) takes row ty of each 32-row slab and the column
+// pairs 2 tx + 32 b' (b' < 4), i.e. columns c_b = 2 tx + 32 (b / 2) + (b % 2), b < 8: one
+// 16-byte shared load brings two adjacent elements (A, B, x hi, x lo alike), and the 16 lanes
+// of a row read 256 contiguous bytes.  Stage release: each warp arrives on empty[s] when it
+// is done with stage s; the producer (thread 0) waits for all 16 before refilling it.
 __global__ void __launch_bounds__(MX_THREADS, 1)
 k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs, int njobs, int mode,
                 GenericIO io, int strided, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smx[];
-  __shared__ uint64_t full[MX_NST];
+  __shared__ uint64_t full[MX_NST], empty[MX_NST];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int lane = tid & 31, warp = tid >> 5;
   const int per = strided ? 1 : (njobs + gridDim.x - 1) / gridDim.x;
   const int t0 = strided ? blockIdx.x : blockIdx.x * per;
   const int t1 = strided ? njobs : min(njobs, t0 + per);
   const int dt = strided ? gridDim.x : 1;
   if (tid == 0) {
-    for (int s = 0; s < MX_NST; ++s)
+    for (int s = 0; s < MX_NST; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mx_s32(&full[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mx_s32(&empty[s])), "r"(MX_WARPS) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -648,15 +641,27 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
   // producer cursor (thread 0): the next (job, slab) to copy, and the active-tile ordinal
   int pt = t0, pa = 0, ptile = 0;
   long long issued = 0;
-  auto produce = [&](long long consumed) {
-    while (issued < consumed + MX_NST) {
+  bool pok = true;
+  // issue every slab below `must` (waiting, bounded, for its stage to be released), then more
+  // while stages happen to be free
+  auto produce = [&](long long must) {
+    while (pok) {
       if (pa == 0) {
         while (pt < t1 && !active(pt)) pt += dt;
         if (pt >= t1) return;
       }
+      const int s = (int)(issued % MX_NST);
+      if (issued >= MX_NST) {     // every warp is done with the previous use of stage s?
+        const uint32_t bar = mx_s32(&empty[s]);
+        const uint32_t par = (uint32_t)(((issued - MX_NST) / MX_NST) & 1);
+        if (issued < must) {
+          if (!mx_wait(bar, par)) { pok = false; return; }
+        } else if (!mx_try(bar, par)) {
+          return;
+        }
+      }
       const TileJob jb = jobs[pt];
       const Prob& p = probs[jb.prob];
-      const int s = (int)(issued % MX_NST);
       const uint32_t bar = mx_s32(&full[s]);
       const uint32_t st = mx_s32(smx) + (uint32_t)s * MX_STAGE;
       const size_t off = ((size_t)jb.t * TS + (size_t)pa * MX_ROWS) * TS;
@@ -666,9 +671,9 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
       mx_copy(st + MX_HALF, (const float2*)p.B + off, MX_HALF, bar);
       if (pa == 0) {   // the tile's two vector chunks, into the x buffer of its parity
         const uint32_t xb = mx_s32(smx) + MX_XOFF + (uint32_t)(ptile & 1) * 2 * MX_XBYTES;
-        const XMix* xs = (const XMix*)p.xs;
-        mx_copy(xb, xs + (int64_t)jb.J * TS, MX_XBYTES, bar);
-        mx_copy(xb + MX_XBYTES, xs + p.Npad + (int64_t)jb.I * TS, MX_XBYTES, bar);
+        const float2* xs = (const float2*)p.xs;
+        mx_copy(xb, xs + (int64_t)jb.J * 2 * TS, MX_XBYTES, bar);
+        mx_copy(xb + MX_XBYTES, xs + (int64_t)jb.I * 2 * TS, MX_XBYTES, bar);
       }
       ++issued;
       if (++pa == MX_SLABS) {
@@ -691,8 +696,11 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
     double sB;
     if (!df_operands(p, mode, io, x, sB)) continue;   // uniform per CTA
     const bool diag = jb.I == jb.J;
-    const XMix* xc = reinterpret_cast<const XMix*>(smx + MX_XOFF + (ctile & 1) * 2 * MX_XBYTES);
-    const XMix* xr = xc + TS;
+    const float2* xcb = reinterpret_cast<const float2*>(smx + MX_XOFF + (ctile & 1) * 2 * MX_XBYTES);
+    const float4* xch = reinterpret_cast<const float4*>(xcb) + tx;          // column chunk J: hi pairs
+    const float4* xcl = reinterpret_cast<const float4*>(xcb + TS) + tx;     //                 lo pairs
+    const float2* xrh = xcb + 2 * TS;                                       // row chunk I: hi
+    const float2* xrl = xrh + TS;                                           //              lo
     // bound m on every |U xh| of this tile (m < 2^(k+1), k its exponent); row chains sum 8
     // such products per lane, column chains 8 (4 rows x 2), so |S| < 2^(k+4) (1 + 3 u); the
     // grid 2^e with e = k + 6 keeps |S| below 2^(e-1) with a factor 2 to spare
@@ -711,38 +719,54 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
 #pragma unroll
     for (int a = 0; a < MX_SLABS; ++a) {
       const int s = (int)(consumed % MX_NST);
+      if (tid == 0) produce(consumed + 1);     // this slab is issued before anyone waits for it
       const bool got = mx_wait(mx_s32(&full[s]), (uint32_t)((consumed / MX_NST) & 1));
-      if (__syncthreads_or(got ? 0 : 1)) { ok = false; break; }
-      const float2* As = reinterpret_cast<const float2*>(smx + (size_t)s * MX_STAGE) + ty * TS + tx;
-      const float2* Bs = As + MX_ROWS * TS;
-      const XMix y = xr[ty + MX_ROWS * a];
+      if (__any_sync(0xffffffffu, !got)) {
+        if (lane == 0) atomicExch(err, 1);
+        ok = false;
+      }
+      if (__syncthreads_or(ok ? 0 : 1)) { ok = false; break; }
+      const float4* As = reinterpret_cast<const float4*>(smx + (size_t)s * MX_STAGE) + ty * (TS / 2) + tx;
+      const float4* Bs = As + MX_ROWS * (TS / 2);
+      // row entry of x_I: (y_re, y_im) and (y_im, -y_re), hi and lo
+      const float2 yh = xrh[ty + MX_ROWS * a], yl = xrl[ty + MX_ROWS * a];
+      const f2 y1h = pk(yh.x, yh.y), y1l = pk(yl.x, yl.y), y2h = pk(yh.y, -yh.x), y2l = pk(yl.y, -yl.x);
+      // chain 1: (U_re x_re, V_re x_im); chain 2: (U_im x_re, V_im x_im)
       f2 H1 = sg2, L1 = zero, H2 = sg2, L2 = zero;
 #pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        const float2 av = As[16 * b], bv = Bs[16 * b];
-        const XMix xv = xc[tx + 16 * b];
-        // (U_re, V_re) and (U_im, V_im), rounded
-        const f2 uvr = fma2(pk(bv.x, bv.x), spm, pk(av.x, av.x));
-        const f2 uvi = fma2(pk(bv.y, bv.y), spm, pk(av.y, av.y));
-        gacc(H1, L1, uvr, xv.h1, xv.l1);
-        gacc(H2, L2, uvi, xv.h2, xv.l2);
-        if (!diag) {
-          gacc(cH[b], cL[b], uvr, y.h1, y.l1);
-          gacc(cH[b], cL[b], uvi, y.h2, y.l2);
+      for (int bp = 0; bp < 4; ++bp) {
+        const float4 a4 = As[16 * bp], b4 = Bs[16 * bp], xh4 = xch[16 * bp], xl4 = xcl[16 * bp];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int b = 2 * bp + e;
+          const float ar = e ? a4.z : a4.x, ai = e ? a4.w : a4.y;
+          const float br = e ? b4.z : b4.x, bi = e ? b4.w : b4.y;
+          const f2 xh = e ? f2hi(xh4) : f2lo(xh4), xl = e ? f2hi(xl4) : f2lo(xl4);
+          // (U_re, V_re) and (U_im, V_im), rounded
+          const f2 uvr = fma2(pk(br, br), spm, pk(ar, ar));
+          const f2 uvi = fma2(pk(bi, bi), spm, pk(ai, ai));
+          gacc(H1, L1, uvr, xh, xl);
+          gacc(H2, L2, uvi, xh, xl);
+          if (!diag) {
+            gacc(cH[b], cL[b], uvr, y1h, y1l);
+            gacc(cH[b], cL[b], uvi, y2h, y2l);
+          }
         }
       }
-      // y_re = lane 0 of chain 1 + lane 1 of chain 2, y_im = lane 1 of 1 + lane 0 of 2;
+      // stage s is no longer read by this warp
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mx_s32(&empty[s])) : "memory");
+      // y_re = U_re x_re - V_im x_im = lane 0 of chain 1 - lane 1 of chain 2,
+      // y_im = V_re x_im + U_im x_re = lane 1 of chain 1 + lane 0 of chain 2;
       // the grid parts add exactly, then (grid, tail) is normalised
       float s1a, s1b, s2a, s2b, l1a, l1b, l2a, l2b;
       upk(sub2(H1, sg2), s1a, s1b);
       upk(sub2(H2, sg2), s2a, s2b);
       upk(L1, l1a, l1b);
       upk(L2, l2a, l2b);
-      two_sum1(__fadd_rn(s1a, s2b), __fadd_rn(l1a, l2b), racc[a].rh, racc[a].rl);
+      two_sum1(__fsub_rn(s1a, s2b), __fsub_rn(l1a, l2b), racc[a].rh, racc[a].rl);
       two_sum1(__fadd_rn(s1b, s2a), __fadd_rn(l1b, l2a), racc[a].ih, racc[a].il);
-      __syncthreads();                 // every thread is done with stage s
       ++consumed;
-      if (tid == 0) produce(consumed);
     }
     if (!ok) break;
     ++ctile;
@@ -770,8 +794,7 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
     }
     if (!diag) {
       // ---- column sums over the 32 row lanes: the two of a warp (xor 16), then 16 warps
-      // in two rounds through an 8 x TS buffer
-      const int lane = tid & 31, warp = tid >> 5;
+      // in two rounds through an 8 x TS buffer.  Column of entry b: 2 tx + 32 (b / 2) + b % 2
       DFC cacc[8];
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
@@ -787,16 +810,17 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
         const DFC snd = up ? cacc[q] : cacc[q + 4], kp = up ? cacc[q + 4] : cacc[q];
         cacc[q] = dfc_add(kp, dfc_shfl(snd, 16));
       }
-      // lane holds columns tx + 16 (q + 4 up), q < 4
+      // lane keeps entries b = q + 4 up, q < 4
+      auto col = [&](int b) { return 2 * tx + 32 * (b >> 1) + (b & 1); };
       if (warp >= 8) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) red[warp - 8][tx + 16 * (q + (up ? 4 : 0))] = cacc[q];
+        for (int q = 0; q < 4; ++q) red[warp - 8][col(q + (up ? 4 : 0))] = cacc[q];
       }
       __syncthreads();
       if (warp < 8) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int c = tx + 16 * (q + (up ? 4 : 0));
+          const int c = col(q + (up ? 4 : 0));
           red[warp][c] = dfc_add(cacc[q], red[warp][c]);
         }
       }
@@ -811,15 +835,13 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
       __syncthreads();                 // red is free for the next tile
     }
   }
-  if (!ok) {
-    if (tid == 0) {
-      atomicExch(err, 1);
-      // nothing may land in shared memory after the CTA exits: wait (bounded) for the copies
-      for (long long g = consumed; g < issued; ++g)
-        mx_wait(mx_s32(&full[g % MX_NST]), (uint32_t)((g / MX_NST) & 1));
-    }
-    __syncthreads();
+  if (tid == 0) {
+    // finish the producer's work only as far as needed to leave no copy in flight
+    if (!ok) pok = false;
+    for (long long g = consumed; g < issued; ++g)
+      mx_wait(mx_s32(&full[g % MX_NST]), (uint32_t)((g / MX_NST) & 1));
   }
+  __syncthreads();
 }
 
 // per-tile bound max over the tile of max(|A_re| + |B_re|, |A_im| + |B_im|)

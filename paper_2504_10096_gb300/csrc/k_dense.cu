@@ -548,7 +548,8 @@ __global__ void __launch_bounds__(256) k_dn_back(const double* __restrict__ Wv, 
 size_t dense_scratch_doubles(int64_t N, int nev) {
   const int64_t n = 2 * N;
   const int64_t ld = (n + 31) / 32 * 32;
-  return (size_t)(2 * ld * n + 4 * n + 8 + (int64_t)nev * (5 * n + n + 2 * n) + 2 * nev + 64);
+  // ten sub-buffers, each rounded up to 32 doubles
+  return (size_t)(2 * ld * n + 4 * n + (int64_t)nev * (5 * n + n + 2 * n) + nev + 8 + 10 * 32);
 }
 
 // Dense diagonalisation of problem 0 of a PH handle: the nev lowest positive omega and
@@ -558,16 +559,23 @@ int dense_shao(const Prob* dprobs, int64_t N, int64_t Npad, bool tiles64, bool p
                int* dflag, double2* Z, double* lam_out, cudaStream_t s) {
   const int64_t n = 2 * N;
   const int64_t ld = (n + 31) / 32 * 32;
-  double* M = work;                 // M_r, then L (lower)
-  double* W = M + ld * n;           // G, then W, then the reduced form with the reflectors
-  double* E = W + ld * n;           // sub-diagonal of T
-  double* T = E + n;                // reflector scalars
-  double* V = T + n;                // current reflector
-  double* Pv = V + n;               // W22 v
-  double* lam = Pv + n + 8;         // wanted eigenvalues of S
-  double* inv = lam + nev + 8;      // inverse-iteration scratch, 5 n per vector
-  double* Sv = inv + (int64_t)nev * 5 * n;
-  double2* qb = reinterpret_cast<double2*>(Sv + (int64_t)nev * n);
+  // sub-buffers start on 256-byte boundaries (q is read and written as double2)
+  size_t off = 0;
+  auto take = [&](int64_t count) {
+    double* p = work + off;
+    off += (size_t)((count + 31) / 32 * 32);
+    return p;
+  };
+  double* M = take(ld * n);         // M_r, then L (lower)
+  double* W = take(ld * n);         // G, then W, then the reduced form with the reflectors
+  double* E = take(n);              // sub-diagonal of T
+  double* T = take(n);              // reflector scalars
+  double* V = take(n);              // current reflector
+  double* Pv = take(n);             // W22 v
+  double* lam = take(nev + 8);      // wanted eigenvalues of S, then the bound of S
+  double* inv = take((int64_t)nev * 5 * n);   // inverse-iteration scratch, 5 n per vector
+  double* Sv = take((int64_t)nev * n);
+  double2* qb = reinterpret_cast<double2*>(take((int64_t)nev * 2 * n));
   if (cudaMemsetAsync(dflag, 0, sizeof(int), s) != cudaSuccess) return -1;
   // 1.
   count_launch();

@@ -708,7 +708,6 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
     const float sg = grid_sigma(m, 6);
     const f2 sg2 = pk(sg, sg);
     const float sgn = sB > 0.0 ? 1.f : -1.f;
-    const f2 spm = pk(sgn, -sgn);
     f2 cH[8], cL[8];
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
@@ -720,12 +719,12 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
     for (int a = 0; a < MX_SLABS; ++a) {
       const int s = (int)(consumed % MX_NST);
       if (tid == 0) produce(consumed + 1);     // this slab is issued before anyone waits for it
-      const bool got = mx_wait(mx_s32(&full[s]), (uint32_t)((consumed / MX_NST) & 1));
-      if (__any_sync(0xffffffffu, !got)) {
+      // a wait that expires raises the error flag; the warp goes on (its reads stay inside
+      // shared memory) and the CTA stops at the end of the tile
+      if (__any_sync(0xffffffffu, !mx_wait(mx_s32(&full[s]), (uint32_t)((consumed / MX_NST) & 1)))) {
         if (lane == 0) atomicExch(err, 1);
         ok = false;
       }
-      if (__syncthreads_or(ok ? 0 : 1)) { ok = false; break; }
       const float4* As = reinterpret_cast<const float4*>(smx + (size_t)s * MX_STAGE) + ty * (TS / 2) + tx;
       const float4* Bs = As + MX_ROWS * (TS / 2);
       // row entry of x_I: (y_re, y_im) and (y_im, -y_re), hi and lo
@@ -742,9 +741,10 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
           const float ar = e ? a4.z : a4.x, ai = e ? a4.w : a4.y;
           const float br = e ? b4.z : b4.x, bi = e ? b4.w : b4.y;
           const f2 xh = e ? f2hi(xh4) : f2lo(xh4), xl = e ? f2hi(xl4) : f2lo(xl4);
-          // (U_re, V_re) and (U_im, V_im), rounded
-          const f2 uvr = fma2(pk(br, br), spm, pk(ar, ar));
-          const f2 uvi = fma2(pk(bi, bi), spm, pk(ai, ai));
+          // (U_re, V_re) and (U_im, V_im), rounded: scalar FMAs straight into the two halves
+          // of a register pair (no lane moves)
+          const f2 uvr = pk(__fmaf_rn(sgn, br, ar), __fmaf_rn(-sgn, br, ar));
+          const f2 uvi = pk(__fmaf_rn(sgn, bi, ai), __fmaf_rn(-sgn, bi, ai));
           gacc(H1, L1, uvr, xh, xl);
           gacc(H2, L2, uvi, xh, xl);
           if (!diag) {
@@ -768,7 +768,10 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
       two_sum1(__fadd_rn(s1b, s2a), __fadd_rn(l1b, l2a), racc[a].ih, racc[a].il);
       ++consumed;
     }
-    if (!ok) break;
+    if (__syncthreads_or(ok ? 0 : 1)) {
+      ok = false;
+      break;
+    }
     ++ctile;
     // ---- row sums: reduce-scatter of the 4 rows over the 16 column lanes, then the
     // remaining pairs; lanes tx % 4 == 0 write row ty + 32 ((tx >> 3) * 2 + ((tx >> 2) & 1))

@@ -1,12 +1,18 @@
 """Benchmark: time to the lowest nev BSE eigenpairs on one GB300.
 
-Workload (one "step" = the whole hot path over one input): the
+Headline workload (one "step" = the whole hot path over one input): the
 pseudo-Hermitian problem of N = 10000 (H of order 20000), complex128,
 lowest 100 positive eigenpairs with the FP64 structure-preserving Lanczos:
 ingest (packing of A and B already resident in HBM) + solve (folded
 products, CGS2, projected eigenproblem, restart/lock, recovery, FP64
-residuals).  The adjoint and the block-product bandwidth are timed as
-separate lines of the same JSON object.
+residuals).  The same JSON line carries, measured in the same run:
+  * "config4": the metric's own configuration -- PH N = 50000, complex64 A
+    and B, lowest 200, residual <= 1e-6 -- solved once on the mixed path and
+    once on the plain FP64 path, with the speed-up and the mixed product's
+    bandwidth (--skip-config4 / --no-config4-fp64 leave it out or shorten it);
+  * the block-product roofline against the FP64 FMA peak measured in the run,
+    the adjoint, the e2e solve through host buffers, and the double-FP32
+    variant of the headline solve.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -525,7 +531,7 @@ def run_workload(args):
         nev = specs[0].nev
         ts = []
         for it in range(args.warmup + args.steps):
-            bs = bse.BatchedSolver(As, Bs, stream=stream)
+            bs = bse.BatchedSolver(As, Bs, stream=stream, mixed=True)   # residual <= 1e-6 needs the mixed path
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize(); e0.record(stream)
             vals, _, nconv = bs.solve(nev, tol=1e-6)
@@ -538,7 +544,7 @@ def run_workload(args):
         if os.path.exists(gold_path):
             gold = np.loadtxt(gold_path).reshape(len(specs), nev)
             err = float(np.max(np.abs(vals - gold) / gold))
-        out.update({"workload": "64 PH problems, N_i in [500,6000], complex64, nev=16, tol 1e-6",
+        out.update({"workload": "64 PH problems, N_i in [500,6000], complex64 (mixed path), nev=16, tol 1e-6",
                     "s_per_batch": statistics.median(ts), "sizes_sum": int(sum(s.n for s in specs)),
                     "max_rel_err_vs_oracle": err, "krylov_steps_total": st["steps"],
                     "passes_total": st["passes"], "launches": st["launches"], "max_residual": st["max_residual"],
@@ -550,7 +556,7 @@ def run_workload(args):
         spec = CONFIGS[3]
         p = make_problem_torch(spec, device="cuda")
         n = args.n or spec.n                       # --n: a principal block (small ncu captures)
-        s = bse.Solver(p["A"][:n, :n].contiguous(), p["B"][:n, :n].contiguous(), stream=stream)
+        s = bse.Solver(p["A"][:n, :n].contiguous(), p["B"][:n, :n].contiguous(), stream=stream, mixed=True)
         del p
         vals, _, _, t_solve = _timed_solve(s, spec.nev, 1e-6, stream, vectors=False)
         g = np.linspace(0.5, 1.5, spec.nev)
@@ -572,7 +578,7 @@ def run_workload(args):
         p = make_problem_torch(spec, device="cuda")
         A, B = p["A"], p["B"]
         nev = spec.nev
-        s = bse.Solver(A, B, stream=stream)
+        s = bse.Solver(A, B, stream=stream, mixed=True)
         vals, _, _, t_solve = _timed_solve(s, nev, 1e-6, stream, vectors=False)
         # FP64 GPU reference on the same complex64 values (targets and gradient reference)
         s64 = bse.Solver(A.to(torch.complex128), B.to(torch.complex128), stream=stream)
@@ -594,7 +600,7 @@ def run_workload(args):
         dA64, dB64 = s64.backward(w + 2.0 * (ref - targets))
         ra = float(torch.linalg.norm((dA.to(torch.complex128) - dA64)) / torch.linalg.norm(dA64))
         rb = float(torch.linalg.norm((dB.to(torch.complex128) - dB64)) / torch.linalg.norm(dB64))
-        out.update({"workload": "PH N=20000 complex64 nev=50, loss sum w*l + sum (l-t)^2",
+        out.update({"workload": "PH N=20000 complex64 (mixed path) nev=50, loss sum w*l + sum (l-t)^2",
                     "solve_s": t_solve, "backward_tc_s": t_bwd, "backward_cuda_cores_s": t_simt,
                     "tc_vs_cuda_cores_rel_diff": tc_vs_simt, "fp64_solve_s": t_ref,
                     "max_rel_eig_err_vs_fp64_gpu": float(np.max(np.abs(vals - ref) / ref)),

@@ -508,8 +508,8 @@ k_prod_tiles_df2(const Prob* __restrict__ probs, const TileJob* __restrict__ job
 // Data movement: one CTA of 512 threads per SM walks its tile jobs; the tile
 // rows stream through a three-stage shared-memory pipeline of 32-row slabs of
 // A and B (64 KiB a stage) filled by bulk asynchronous copies (cp.async.bulk,
-// completion counted on an mbarrier), so ~190 KiB per SM are in flight while
-// the registers hold only accumulators.  The vector enters pre-split
+// completion counted on an mbarrier), so up to 192 KiB per SM are in flight
+// while the registers hold only accumulators.  The vector enters pre-split
 // (k_mx_stage_x, once per product: hi/lo pairs in both pairings, and the max
 // |xh| of every 128-entry chunk) and its two chunks ride along with a tile's
 // first slab.  Every wait is bounded: on expiry the CTA stops, waits (bounded)

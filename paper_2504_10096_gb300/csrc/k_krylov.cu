@@ -314,15 +314,10 @@ k_normalize(const Prob* __restrict__ probs, int ph, int start) {
   }
 }
 
-// Record alpha_j, beta_j, advance j.  fresh = 0: regular step; fresh = 1:
-// a first or replacement vector was just normalised.  One thread per problem.
-__global__ void k_step_finish(const Prob* __restrict__ probs, int nprob, int ph, int fresh) {
-  const int ip = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ip >= nprob) return;
-  const Prob& p = probs[ip];
+// Record alpha_j, beta_j, advance j, given beta^2 = b2 of the new vector.  fresh = 0:
+// regular step; fresh = 1: a first or replacement vector was just normalised.
+__device__ void step_finish_one(const Prob& p, int ph, int fresh, double b2) {
   KState* st = p.st;
-  if (!kphase(st, fresh)) return;
-  const double b2 = sum_norm_parts(p);
   const int j = st->j;
   if (!fresh) {
     const double2* coef = (const double2*)p.coef;
@@ -352,6 +347,59 @@ __global__ void k_step_finish(const Prob* __restrict__ probs, int nprob, int ph,
     st->j = j + 1;
   }
   if (st->steps >= st->maxit && !st->done) { st->done = 1; st->status = ST_NOCONV; }
+}
+
+// One thread per problem.
+__global__ void k_step_finish(const Prob* __restrict__ probs, int nprob, int ph, int fresh) {
+  const int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= nprob) return;
+  const Prob& p = probs[ip];
+  if (!kphase(p.st, fresh)) return;
+  step_finish_one(p, ph, fresh, sum_norm_parts(p));
+}
+
+// Problems of at most one reduction row block (Npad <= ROWBLK): the norm, the scaling of
+// the new basis vector and the state update in one CTA per problem (one launch instead of
+// three per Krylov step; the same arithmetic as k_norm_partial, k_normalize, k_step_finish).
+template <typename ST>
+__global__ void __launch_bounds__(256)
+k_norm_fused(const Prob* __restrict__ probs, int ph, int start) {
+  using R = typename RealOf<ST>::T;
+  __shared__ double red[8];
+  __shared__ double sb2;
+  const Prob& p = probs[blockIdx.x];
+  const KState* st = p.st;
+  if (!kphase(st, start)) return;
+  const ST* w = (const ST*)p.w;
+  const ST* pw = (const ST*)(ph ? p.pw : p.w);
+  double s = 0.0;
+  for (int64_t r = threadIdx.x; r < p.Npad; r += 256) {
+    const ST a = w[r], b = pw[r];
+    s += (double)a.x * (double)b.x + (double)a.y * (double)b.y;
+  }
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += red[i];
+    sb2 = t;
+  }
+  __syncthreads();
+  const double b2 = sb2;
+  if (b2 > 0.0 && isfinite(b2)) {
+    const R inv = (R)(1.0 / sqrt(b2));
+    const int col = st->j + 1;
+    ST* V = (ST*)p.V + (int64_t)col * p.Npad;
+    ST* P = ph ? (ST*)p.P + (int64_t)col * p.Npad : nullptr;
+    for (int64_t r = threadIdx.x; r < p.Npad; r += 256) {
+      V[r] = cscale(w[r], inv);
+      if (ph) P[r] = cscale(((const ST*)p.pw)[r], inv);
+    }
+  }
+  __syncthreads();                     // every thread has read st->j
+  if (threadIdx.x == 0) step_finish_one(p, ph, start, b2);
 }
 
 // ---------------------------------------------------------------- start vector
@@ -503,6 +551,11 @@ void launch_step_cgs(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t 
 template <typename ST>
 void launch_step_normalize(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t maxNpad,
                            int start, cudaStream_t s) {
+  if (maxnrb == 1) {
+    count_launch();
+    k_norm_fused<ST><<<nprob, 256, 0, s>>>(dprobs, ph, start);
+    return;
+  }
   count_launch(3);
   // start: 0 regular step, 1 fresh (first or replacement) vector
   k_norm_partial<ST><<<dim3(maxnrb, nprob), 256, 0, s>>>(dprobs, ph, start);

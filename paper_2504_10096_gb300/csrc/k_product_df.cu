@@ -501,9 +501,12 @@ k_prod_tiles_df2(const Prob* __restrict__ probs, const TileJob* __restrict__ job
 //     and Oishi, "Accurate floating-point summation", 2008, used here as an
 //     accumulator).  Five packed f32x2 instructions per pair of
 //     multiply-accumulates, against twelve for Dekker's product and Knuth's
-//     TwoSum in k_prod_tiles_df2; the chain error is about 2^-35 of
-//     max|U| max|xh| (the tail's own FP32 rounding), so tiles with big
-//     entries stay on k_prod_tiles_df2.
+//     TwoSum in k_prod_tiles_df2.  The cross-lane sums of a tile use the same
+//     idea one level up: every chain value is split at a grid 2^5 coarser than
+//     the chains' (regrid), so the 16 or 32 grid parts of a row or column add
+//     exactly with plain FP32 adds and only the tails round.  The error is
+//     about 2^-30 of max|U| max|xh| in the worst case (the tails' FP32
+//     rounding), so tiles with big entries stay on k_prod_tiles_df2.
 //
 // Data movement: one CTA of 512 threads per SM walks its tile jobs; the tile
 // rows stream through a three-stage shared-memory pipeline of 32-row slabs of
@@ -535,6 +538,23 @@ __device__ __forceinline__ void two_sum1(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   const float bp = __fsub_rn(s, a);
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+// (grid part, tail) pairs of the coarse kernel's cross-lane sums: the grid parts of all lanes
+// lie on one grid coarse enough that their sums are exact, so the pairs add with plain adds
+__device__ __forceinline__ DFC gadd(DFC a, const DFC& b) {
+  a.rh = __fadd_rn(a.rh, b.rh);
+  a.rl = __fadd_rn(a.rl, b.rl);
+  a.ih = __fadd_rn(a.ih, b.ih);
+  a.il = __fadd_rn(a.il, b.il);
+  return a;
+}
+
+// split an exact chain value S (|S| < 2^e, on the grid 2^(e-23)) at the grid of gs = 1.5 2^(e+5):
+// g = the part on the grid 2^(e-18) (exact), and the rest (|.| <= 2^(e-19), exact) added to l
+__device__ __forceinline__ void regrid(float S, float l, float gs, float& g, float& lo) {
+  g = __fsub_rn(__fadd_rn(gs, S), gs);
+  lo = __fadd_rn(l, __fsub_rn(S, g));
 }
 
 // x of every active problem, split once per product into chunks of 128 entries,
@@ -707,6 +727,9 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
     const float m = p.tmax[jb.t] * fmaxf(p.xmax[jb.I], p.xmax[jb.J]);
     const float sg = grid_sigma(m, 6);
     const f2 sg2 = pk(sg, sg);
+    // grid of the cross-lane sums: a lane's chain values are below 2^e, at most 32 of them are
+    // added, and 1.5 2^(e+5) leaves a factor 4 to spare (e = k + 6 of the chain grid)
+    const float gs = grid_sigma(m, 11);
     const float sgn = sB > 0.0 ? 1.f : -1.f;
     f2 cH[8], cL[8];
 #pragma unroll
@@ -764,8 +787,8 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
       upk(sub2(H2, sg2), s2a, s2b);
       upk(L1, l1a, l1b);
       upk(L2, l2a, l2b);
-      two_sum1(__fsub_rn(s1a, s2b), __fsub_rn(l1a, l2b), racc[a].rh, racc[a].rl);
-      two_sum1(__fadd_rn(s1b, s2a), __fadd_rn(l1b, l2a), racc[a].ih, racc[a].il);
+      regrid(__fsub_rn(s1a, s2b), __fsub_rn(l1a, l2b), gs, racc[a].rh, racc[a].rl);
+      regrid(__fadd_rn(s1b, s2a), __fadd_rn(l1b, l2a), gs, racc[a].ih, racc[a].il);
       ++consumed;
     }
     if (__syncthreads_or(ok ? 0 : 1)) {
@@ -780,15 +803,15 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const DFC snd = u8 ? racc[q] : racc[q + 2], kp = u8 ? racc[q + 2] : racc[q];
-        racc[q] = dfc_add(kp, dfc_shfl(snd, 8));
+        racc[q] = gadd(kp, dfc_shfl(snd, 8));
       }
       const bool u4 = tx & 4;
       {
         const DFC snd = u4 ? racc[0] : racc[1], kp = u4 ? racc[1] : racc[0];
-        racc[0] = dfc_add(kp, dfc_shfl(snd, 4));
+        racc[0] = gadd(kp, dfc_shfl(snd, 4));
       }
-      racc[0] = dfc_add(racc[0], dfc_shfl(racc[0], 2));
-      racc[0] = dfc_add(racc[0], dfc_shfl(racc[0], 1));
+      racc[0] = gadd(racc[0], dfc_shfl(racc[0], 2));
+      racc[0] = gadd(racc[0], dfc_shfl(racc[0], 1));
       if ((tx & 3) == 0) {
         const int a = (u8 ? 2 : 0) + (u4 ? 1 : 0);
         float4* part = (float4*)p.part;
@@ -804,14 +827,14 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
         float hr, hi, lr, li;
         upk(sub2(cH[b], sg2), hr, hi);
         upk(cL[b], lr, li);
-        two_sum1(hr, lr, cacc[b].rh, cacc[b].rl);
-        two_sum1(hi, li, cacc[b].ih, cacc[b].il);
+        regrid(hr, lr, gs, cacc[b].rh, cacc[b].rl);
+        regrid(hi, li, gs, cacc[b].ih, cacc[b].il);
       }
       const bool up = lane & 16;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const DFC snd = up ? cacc[q] : cacc[q + 4], kp = up ? cacc[q + 4] : cacc[q];
-        cacc[q] = dfc_add(kp, dfc_shfl(snd, 16));
+        cacc[q] = gadd(kp, dfc_shfl(snd, 16));
       }
       // lane keeps entries b = q + 4 up, q < 4
       auto col = [&](int b) { return 2 * tx + 32 * (b >> 1) + (b & 1); };
@@ -824,14 +847,14 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int c = col(q + (up ? 4 : 0));
-          red[warp][c] = dfc_add(cacc[q], red[warp][c]);
+          red[warp][c] = gadd(cacc[q], red[warp][c]);
         }
       }
       __syncthreads();
       if (tid < TS) {
         DFC sum = red[0][tid];
 #pragma unroll
-        for (int w = 1; w < 8; ++w) sum = dfc_add(sum, red[w][tid]);
+        for (int w = 1; w < 8; ++w) sum = gadd(sum, red[w][tid]);
         float4* part = (float4*)p.part;
         part[((int64_t)jb.J * p.nT + jb.I) * TS + tid] = dfc_pack(sum);
       }

@@ -116,3 +116,19 @@ def test_more_validation_without_gpu(lib):
     assert noalloc(10, dummy, dummy, bse.BSE_C128_DF, 1, dummy, dummy) == bse.BSE_EINVAL
     assert noalloc(10, dummy, dummy, 1, 1, None, dummy) == bse.BSE_EINVAL
     assert noalloc(10, dummy, dummy, 1, 1, dummy, None) == bse.BSE_EINVAL
+
+
+def test_newer_entry_points_validate_without_gpu(lib):
+    """The dense solve, the mixed product, the residual query and the FP64 peak
+    measurement reject bad arguments before any CUDA call."""
+    from paper_2504_10096_gb300 import bse
+    dummy = ctypes.c_void_p(16)
+    ev = (ctypes.c_double * 4)()
+    n = ctypes.c_int(0)
+    assert lib.bse_solve_dense(None, 4, 1e-10, ev, None, ctypes.byref(n)) == bse.BSE_EINVAL
+    assert lib.bse_apply_mixed(None, bse.BSE_OP_MPLUS, 0.0, dummy, dummy) == bse.BSE_EINVAL
+    assert lib.bse_get_residuals(None, 0, ev, 4) == bse.BSE_EINVAL
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    assert lib.bse_measure_fp64_peak(0, ctypes.byref(tf), ctypes.byref(ms)) == bse.BSE_EINVAL
+    assert lib.bse_measure_fp64_peak(1 << 25, ctypes.byref(tf), ctypes.byref(ms)) == bse.BSE_EINVAL
+    assert lib.bse_measure_fp64_peak(100, None, None) == bse.BSE_EINVAL

@@ -169,12 +169,14 @@ def test_config3r_finite_differences_seven_directions():
     assert worst <= 1e-5, worst
 
 
-@pytest.mark.parametrize("tol,bound", [(1e-10, 1e-5), (1e-6, 5e-2)])
+@pytest.mark.parametrize("tol,bound", [(1e-10, 1e-5), (1e-6, 1e-4)])
 def test_config3r_mixed_tensor_core_gradient(tol, bound):
     """Mixed path (complex64 storage, FP64 basis, double-FP32 products) with the
     tcgen05 3xTF32 adjoint, against the stored FP64 oracle gradient.  The error
-    is the eigenvectors' (tol |omega| / gap, gaps down to ~1e-5 eV here) plus
-    the 3xTF32 / complex64-output floor (~1e-6): the stated bounds."""
+    is the eigenvectors' (at most tol |omega| / gap, gaps down to ~1e-5 eV here)
+    plus the 3xTF32 / complex64-output floor (~1e-6): measured 1.5e-6 at both
+    tolerances (the residuals reached are far below tol); stated bounds 1e-5 and
+    1e-4 of the largest probed entry."""
     from paper_2504_10096_gb300 import bse
     spec, A, B, gold, probes, Gref, w, t = _config3r()
     s = bse.Solver(_dev(A), _dev(B), mixed=True)

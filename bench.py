@@ -494,7 +494,8 @@ def run_workload(args):
     batch -- 64 pseudo-Hermitian problems, N_i ~ U{500..6000}, complex64, 16 each
     adjoint -- N = 20000, complex64, lowest 50, solve + Hellmann-Feynman backward
     mixed -- N = 50000, complex64 (mixed path) vs complex128 (FP64 path), lowest 200, tol 1e-6
-    haydock -- N = 10000 pseudo-Hermitian, complex128, Lanczos-Haydock spectrum (600 steps)"""
+    haydock -- N = 10000 pseudo-Hermitian, complex128, Lanczos-Haydock spectrum (600 steps)
+    variants -- config 1 with each structure-preserving Lanczos variant (Shao, Gruning, projected BSE)"""
     import torch
     from paper_2504_10096_gb300 import bse
     from synthetic import CONFIGS, batched_specs, loss_draws, make_problem, make_problem_torch, random_start
@@ -522,6 +523,36 @@ def run_workload(args):
                     "krylov_steps": st["steps"], "max_residual": st["max_residual"], "launches": st["launches"],
                     "product_shape": {"ctas_per_sm": st["shape_ctas_per_sm"], "strided": st["shape_strided"],
                                       "tuned": st["tuned"]}})
+    elif args.mode == "variants":
+        # config 1 (PH N = 10^4 complex128, lowest 100, FP64, tol 1e-12) with each of the three
+        # structure-preserving Lanczos variants on one handle (ingest outside the timed solves)
+        spec = CONFIGS[1]
+        p = make_problem_torch(spec, device="cuda")
+        s = bse.Solver(p["A"], p["B"], stream=stream)
+        del p
+        gold_path = os.path.join(ROOT, "tests", "golden", "config1_omega.txt")
+        gold = np.loadtxt(gold_path) if os.path.exists(gold_path) else None
+        names = {"shao": bse.BSE_VARIANT_SHAO, "gruning": bse.BSE_VARIANT_GRUNING,
+                 "projected": bse.BSE_VARIANT_PROJECTED}
+        res = {}
+        for name, v in names.items():
+            ts = []
+            for it in range(args.warmup + max(1, args.steps)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(); e0.record(stream)
+                vals, _, nconv = s.solve(spec.nev, tol=1e-12, vectors=True, variant=v)
+                e1.record(stream); torch.cuda.synchronize()
+                if it >= args.warmup:
+                    ts.append(e0.elapsed_time(e1) / 1e3)
+            st = s.stats()
+            res[name] = {"s_per_solve": statistics.median(ts), "nconv": int(nconv), "steps": st["steps"],
+                         "passes": st["passes"], "restarts": st["restarts"], "launches": st["launches"],
+                         "ms_product": st["ms_product"], "max_residual": st["max_residual"],
+                         "max_rel_err_vs_oracle": (float(np.max(np.abs(vals - gold) / gold))
+                                                   if gold is not None else None)}
+        s.close()
+        out.update({"workload": "config 1: PH N=10000 complex128, nev=100, tol 1e-12, FP64, per variant",
+                    "variants": res})
     elif args.mode == "batch":
         specs = batched_specs()
         As, Bs = [], []
@@ -695,6 +726,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--mode", default="solve", choices=["solve", "product", "tda", "batch", "adjoint", "mixed",
+                                                        "variants",
                                                               "haydock", "profile", "backward"])
     ap.add_argument("--n", type=int, default=0, help="product mode: N (default 8000); mixed mode: principal "
                                                        "block of the config-4 matrices (default: all of it)")

@@ -91,6 +91,31 @@ typedef enum bse_op {
   BSE_OP_H = 3        /* Y = H X, X and Y stacked (X1; X2), 2N rows         */
 } bse_op;
 
+/* Structure-preserving Lanczos variants for BSE_PH handles (Sec. 2.2.1 lists
+   three variations of a structure-preserving thick-restart Lanczos).  All
+   build the Krylov space of H from an even start vector (u; conj(u)), work
+   only with the top halves of the basis (the lower blocks are implicit), use
+   two structured products per step and return the same eigenpairs; they
+   differ in the recurrence, its inner product and the projected problem:
+     SHAO       the folded recurrence on M- M+ (M+- u = A u +- B conj(u)) in
+                the inner product Re(x^H M+ y); projected matrix of omega^2
+                (arrowhead + tridiagonal), solved by bisection and inverse
+                iteration; omega recovered at the end;
+     GRUNING    the Lanczos recurrence of H itself in the M inner product of
+                Eq. 2, alternating even and odd vectors (two bases, two
+                Gram-Schmidt passes per step); projected matrix with zero
+                diagonal whose eigenvalues are +-omega directly;
+     PROJECTED  the folded recurrence, with the projected problem written as
+                a small BSE matrix [[A_k, B_k], [-B_k, -A_k]] (A_k, B_k real
+                symmetric) and solved at every restart by the dense
+                structure-preserving method of Sec. 2.1.1 on the GPU.
+   TDA handles run the plain Hermitian Lanczos recurrence for every value. */
+typedef enum bse_variant {
+  BSE_VARIANT_SHAO = 0,
+  BSE_VARIANT_GRUNING = 1,
+  BSE_VARIANT_PROJECTED = 2
+} bse_variant;
+
 /* Solver options.  Zero-initialise and set what you need; zero fields take
    the defaults given in brackets. */
 typedef struct bse_solve_opts {
@@ -121,6 +146,7 @@ typedef struct bse_solve_opts {
                          If a solve with coarse tiles leaves a pair above tol
                          on the FP64 residual check before maxit, it is
                          repeated with every tile exact (retried_exact).      */
+  int variant;        /* bse_variant; values outside it: BSE_EINVAL [SHAO]    */
 } bse_solve_opts;
 
 /* Per-solve counters, filled by bse_get_stats after a solve. */

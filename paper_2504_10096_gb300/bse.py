@@ -30,13 +30,15 @@ EXPORTED = ["bse_strerror", "bse_create", "bse_create_batched", "bse_solve", "bs
             "bse_apply_noalloc", "bse_backward_ex", "bse_haydock", "bse_selftest_bounded_wait",
             "bse_get_residuals", "bse_apply_mixed", "bse_measure_fp64_peak", "bse_solve_dense"]
 BSE_IMPL_AUTO, BSE_IMPL_CUDA_CORES, BSE_IMPL_TENSOR_CORES = 0, 1, 2
+BSE_VARIANT_SHAO, BSE_VARIANT_GRUNING, BSE_VARIANT_PROJECTED = 0, 1, 2
 BSE_NOALLOC_MAX_N = 4096
 
 
 class bse_solve_opts(ctypes.Structure):
     _fields_ = [("ncv", ctypes.c_int), ("maxit", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("v0", ctypes.c_void_p), ("lock_tol", ctypes.c_double),
-                ("stream_launches", ctypes.c_int), ("tile_tau", ctypes.c_double)]
+                ("stream_launches", ctypes.c_int), ("tile_tau", ctypes.c_double),
+                ("variant", ctypes.c_int)]
 
 
 class bse_stats(ctypes.Structure):
@@ -304,7 +306,7 @@ class Solver:
         self.nev = 0
 
     def solve(self, nev, tol=None, ncv=0, maxit=0, seed=0, vectors=True, lock_tol=0.0, check=True,
-              graphs=True, v0=None, tile_tau=0.0):
+              graphs=True, v0=None, tile_tau=0.0, variant=BSE_VARIANT_SHAO):
         torch = _torch()
         if tol is None:
             tol = 1e-12 if self.dtype == BSE_C128 else 1e-6
@@ -316,7 +318,8 @@ class Solver:
             bdt = torch.complex64 if self.dtype == BSE_C64 else torch.complex128
             v0t = torch.as_tensor(v0).to(device=self.device, dtype=bdt).contiguous()
         opts = bse_solve_opts(ncv=ncv, maxit=maxit, seed=seed, v0=v0t.data_ptr() if v0t is not None else None,
-                              lock_tol=lock_tol, stream_launches=0 if graphs else 1, tile_tau=tile_tau)
+                              lock_tol=lock_tol, stream_launches=0 if graphs else 1, tile_tau=tile_tau,
+                              variant=variant)
         rc, vals, nconv = bse_solve_ex(self.h, nev, tol, BSE_LOWEST, opts,
                                        ev.data_ptr() if ev is not None else None)
         if check:
@@ -410,12 +413,13 @@ class BatchedSolver:
                                     BSE_PH, self.dtype, BSE_DEVICE, self.stream.cuda_stream)
         self.As = self.Bs = None      # the library holds its own packed copies
 
-    def solve(self, nev, tol=1e-6, ncv=0, maxit=0, vectors=False, check=True, graphs=True, tile_tau=0.0):
+    def solve(self, nev, tol=1e-6, ncv=0, maxit=0, vectors=False, check=True, graphs=True, tile_tau=0.0,
+              variant=BSE_VARIANT_SHAO):
         torch = _torch()
         vecs = [torch.empty((nev, 2 * n), dtype=self.cdtype, device=self.device) for n in self.Ns] \
             if vectors else None
         opts = bse_solve_opts(ncv=ncv, maxit=maxit, seed=0, v0=None, lock_tol=0.0,
-                              stream_launches=0 if graphs else 1, tile_tau=tile_tau)
+                              stream_launches=0 if graphs else 1, tile_tau=tile_tau, variant=variant)
         rc, vals, nconv = bse_solve_batched(self.h, len(self.Ns), nev, tol, BSE_LOWEST, opts,
                                             [v.data_ptr() for v in vecs] if vecs else None)
         if check:

@@ -39,6 +39,10 @@ struct ProbHost {
   void* xs = nullptr;        // mixed PH path: pre-split product vector and chunk maxima
   float* xmax = nullptr;
   double *cpart = nullptr, *coef = nullptr, *small = nullptr, *S = nullptr;
+  // Gruning variant: odd basis W, Z = M- W, their restart scratch, the projected tree and the
+  // odd-side Ritz coefficients (allocated by the first solve that asks for the variant)
+  void *W = nullptr, *Z2 = nullptr, *Zo = nullptr, *W2 = nullptr;
+  double *jw = nullptr, *S2 = nullptr;
   // results
   double2* Z = nullptr;
   int zcols = 0;
@@ -140,6 +144,13 @@ struct bse_handle {
   int sg_ncv = 0;
   bool graphs = true;
   cudaStream_t cap = nullptr;
+  // structure-preserving variant of the current solve (PH handles) and the scratch of the
+  // projected-BSE variant's dense solves
+  int variant = 0;
+  int sg_variant = 0;        // variant of the captured graphs
+  double* pj_work = nullptr;
+  size_t pj_doubles = 0;
+  int* pj_flag = nullptr;
 };
 
 namespace {
@@ -178,6 +189,7 @@ void free_solve_buffers(ProbHost& q) {
   dfree(q.V); dfree(q.P); dfree(q.V2); dfree(q.P2); dfree(q.w); dfree(q.pw); dfree(q.part); dfree(q.xs);
   dfreet(q.xmax);
   dfreet(q.cpart); dfreet(q.coef); dfreet(q.small); dfreet(q.S);
+  dfree(q.W); dfree(q.Zo); dfree(q.W2); dfree(q.Z2); dfreet(q.jw); dfreet(q.S2);
   q.ncv = 0;
 }
 
@@ -311,17 +323,36 @@ struct Driver {
     }
   }
 
-  void cgs(int pass) {
+  bool gruning() const { return h->ph && h->variant == VAR_GRUNING; }
+
+  void cgs(int pass, int half = 0) {
     const int ncol = h->ncv + 1 + h->ncv;
-    launch_step_cgs<ST>(h->dprobs, h->count, h->ph, h->maxnrb, h->maxNpad, ncol, pass, s);
+    launch_step_cgs<ST>(h->dprobs, h->count, h->ph, h->maxnrb, h->maxNpad, ncol, pass, half, s);
+  }
+
+  void normalize(int start, int half, cudaStream_t st) {
+    launch_step_normalize<ST>(h->dprobs, h->count, h->ph, h->maxnrb, h->maxNpad, start, half, st);
   }
 
   void step() {
+    if (gruning()) {
+      // odd half: r = p_j against W and i V, pw = M- r, alpha_j, w_j = r / alpha_j, z_j
+      cgs(0, 1);
+      cgs(1, 1);
+      product(PM_STEP_MMINUS_W);
+      normalize(0, 1, s);
+      // even half: s = z_j against V and i W, pw = M+ s, beta_j, u_{j+1}, p_{j+1}
+      cgs(0, 2);
+      cgs(1, 2);
+      product(PM_STEP_MPLUS);
+      normalize(0, 2, s);
+      return;
+    }
     product(h->ph ? PM_STEP_MMINUS : PM_STEP_A);
     cgs(0);
     cgs(1);
     if (h->ph) product(PM_STEP_MPLUS);
-    launch_step_normalize<ST>(h->dprobs, h->count, h->ph, h->maxnrb, h->maxNpad, 0, s);
+    normalize(0, 0, s);
   }
 
   // record 2^b steps into h->sg[b]; false (and graphs off for the handle)
@@ -397,9 +428,27 @@ struct Driver {
   }
 
   void restart_seq(cudaStream_t st) {
-    launch_ritz(h->dprobs, h->count, h->ncv, st);
+    launch_ritz(h->dprobs, h->count, h->ncv, gruning(), st);
     launch_lock_decide_form(h->dprobs, h->count, h->ph, st);
-    launch_restart<ST>(h->dprobs, h->count, h->ph, h->maxNpad, h->ncv, st);
+    launch_restart<ST>(h->dprobs, h->count, h->ph, h->maxNpad, h->ncv, gruning(), st);
+  }
+
+  // projected-BSE variant: each active problem's projected matrix goes through the dense
+  // structure-preserving solver (sizes from the Krylov state just read), then the same lock
+  // decision and restart as the folded iteration; launched on the stream, not captured
+  int run_restart_projected() {
+    for (int i = 0; i < h->count; ++i) {
+      const KState& st = h->hstate[i];
+      if (st.done || st.status != ST_OK) continue;
+      const int n = st.m - st.k;
+      const int nw = std::min(st.r_pkeep - st.k, n);
+      const int rc = projected_ritz(h->dprobs, i, n, nw, h->pj_work, h->pj_flag, h->stream);
+      if (rc < 0) return BSE_ECUDA;
+    }
+    launch_lock_decide_form(h->dprobs, h->count, h->ph, h->stream);
+    launch_restart<ST>(h->dprobs, h->count, h->ph, h->maxNpad, h->ncv, false, h->stream);
+    CK(cudaGetLastError());
+    return BSE_OK;
   }
 
   // the restart sequence reads every decision from KState, so it replays as
@@ -442,11 +491,13 @@ struct Driver {
   }
 
   void fresh_chain(uint64_t seed, const void* v0) {
+    // a fresh vector is even on the Gruning path: against V and the twins i W
+    const int half = gruning() ? 2 : 0;
     launch_start_vector<ST>(h->dprobs, h->count, h->maxNpad, seed, v0, h->stream);
-    cgs(2);
-    cgs(3);
+    cgs(2, half);
+    cgs(3, half);
     if (h->ph) product(PM_START_MPLUS);
-    launch_step_normalize<ST>(h->dprobs, h->count, h->ph, h->maxnrb, h->maxNpad, 1, h->stream);
+    normalize(1, half, h->stream);
   }
 
   int read_state() {
@@ -489,6 +540,10 @@ struct Driver {
       }
       if (steps > 0) {
         run_steps(steps);
+        continue;
+      }
+      if (h->ph && h->variant == VAR_PROJECTED) {
+        if ((rc = run_restart_projected())) return rc;
         continue;
       }
       run_restart();
@@ -630,6 +685,36 @@ int alloc_solve(bse_handle* h, int ncv) {
     CK(cudaMemsetAsync(q.S, 0, sizeof(double) * (size_t)ncv * ncv, h->stream));
     q.ncv = ncv;
   }
+  if (h->ph && h->variant == VAR_GRUNING) {
+    for (int i = 0; i < h->count; ++i) {
+      ProbHost& q = h->p[i];
+      if (q.W) continue;
+      const size_t vb = es * (size_t)q.Npad * ncv;
+      const size_t jwld = 2 * (size_t)ncv + 2;
+      int rc;
+      if ((rc = dalloc(&q.W, vb)) || (rc = dalloc(&q.Zo, vb)) || (rc = dalloc(&q.W2, vb)) ||
+          (rc = dalloc(&q.Z2, vb)) || (rc = dalloc((void**)&q.jw, sizeof(double) * jwld * (4 + (size_t)ncv))) ||
+          (rc = dalloc((void**)&q.S2, sizeof(double) * (size_t)ncv * ncv)))
+        return rc;
+      CK(cudaMemsetAsync(q.W, 0, vb, h->stream));
+      CK(cudaMemsetAsync(q.Zo, 0, vb, h->stream));
+      CK(cudaMemsetAsync(q.S2, 0, sizeof(double) * (size_t)ncv * ncv, h->stream));
+    }
+  }
+  if (h->ph && h->variant == VAR_PROJECTED) {
+    const size_t need = (dense_scratch_doubles(ncv, ncv) + 31) / 32 * 32 + projected_scratch_doubles(ncv, ncv);
+    if (need > h->pj_doubles) {
+      dfreet(h->pj_work);
+      h->pj_doubles = 0;
+      int rc = dalloc((void**)&h->pj_work, sizeof(double) * need);
+      if (rc) return rc;
+      h->pj_doubles = need;
+    }
+    if (!h->pj_flag) {
+      int rc = dalloc((void**)&h->pj_flag, sizeof(int));
+      if (rc) return rc;
+    }
+  }
   return BSE_OK;
 }
 
@@ -664,6 +749,11 @@ int upload_probs(bse_handle* h) {
     d.tmax = q.tmax;
     d.xs = q.xs;
     d.xmax = q.xmax;
+    d.variant = h->ph ? h->variant : VAR_SHAO;
+    d.W = q.W; d.Z = q.Zo; d.W2 = q.W2; d.Z2 = q.Z2;
+    d.jw = q.jw;
+    d.jwld = 2 * q.ncv + 2;
+    d.S2 = q.S2;
   }
   CK(cudaMemcpyAsync(h->dprobs, h->hprobs.data(), sizeof(Prob) * h->count, cudaMemcpyHostToDevice,
                      h->stream));
@@ -736,6 +826,13 @@ int solve_impl(bse_handle* h, int nev, double tol, const bse_solve_opts* opts, d
   const double lock_tol = opts && opts->lock_tol > 0.0 ? opts->lock_tol : tol * 0.25;
   const void* v0 = (opts && h->count == 1) ? opts->v0 : nullptr;
   const bool graphs = !(opts && opts->stream_launches);
+  const int variant = opts ? opts->variant : BSE_VARIANT_SHAO;
+  if (variant < BSE_VARIANT_SHAO || variant > BSE_VARIANT_PROJECTED) return BSE_EINVAL;
+  h->variant = h->ph ? variant : BSE_VARIANT_SHAO;
+  if (h->variant != h->sg_variant) {          // the captured graphs hold one variant's kernels
+    Driver<ST>(h).drop_graphs();
+    h->sg_variant = h->variant;
+  }
   int rc = alloc_solve(h, ncv);
   if (rc) return rc;
   const double tau_opt = opts ? opts->tile_tau : 0.0;
@@ -1537,6 +1634,8 @@ int bse_destroy(bse_handle* h) {
   dfreet(h->dstate);
   dfreet(h->djobs);
   dfree(h->post);
+  dfreet(h->pj_work);
+  dfreet(h->pj_flag);
   dfreet(h->adj_tiles);
   dfreet(h->adj_tiles128);
   dfree(h->adj_panels);

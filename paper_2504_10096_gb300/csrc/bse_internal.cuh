@@ -85,6 +85,15 @@ struct KState {
   double beta_last;   // beta_{m-1}: coupling of the last vector to V[:, m]
 };
 
+// Structure-preserving Lanczos variants of the pseudo-Hermitian iteration
+// (Sec. 2.2.1 names three): VAR_SHAO, the folded recurrence on M- M+ in the
+// M+ inner product; VAR_GRUNING, the Lanczos recurrence of H itself in the
+// M inner product (even and odd basis vectors, projected matrix with a zero
+// diagonal, eigenvalues +-omega); VAR_PROJECTED, the folded recurrence with
+// the projected problem written as a small BSE matrix and solved by the
+// dense structure-preserving method of Sec. 2.1.1.
+enum Variant : int { VAR_SHAO = 0, VAR_GRUNING = 1, VAR_PROJECTED = 2 };
+
 // Static description of one problem (device resident, read-only in kernels).
 struct Prob {
   int64_t N;
@@ -123,6 +132,18 @@ struct Prob {
   const float* tmax;
   void* xs;           // mixed PH path: the pre-split vector of a product, 2 x Npad x 32 B
   float* xmax;        // ... and the max |hi part| of each 128-entry chunk [nT]
+  int variant;        // Variant (PH handles; TDA runs the plain Lanczos recurrence)
+  // VAR_GRUNING: the odd basis W (tops of the odd vectors (w; -conj(w))), Npad x ncv,
+  // its image Z = M- W, their restart scratch, the projected tree of H (jw: four arrays
+  // of jwld entries -- leaf values, leaf couplings, hub/tail diagonal, tail couplings --
+  // then its Ritz vectors, jwld x ncv), and the odd-side Ritz coefficients S2 (ncv x ncv)
+  void* W;
+  void* Z;
+  void* W2;
+  void* Z2;
+  double* jw;
+  int jwld;           // 2 ncv + 2
+  double* S2;
 };
 
 // Jobs of the tiled product: problem, tile row I, tile column J, tile index.
@@ -135,6 +156,7 @@ enum ProdMode : int {
   PM_STEP_A = 2,       // w  = A v_j                   (TDA step)
   PM_START_MPLUS = 3,  // pw = A w + B conj(w) at start / new-vector time
   PM_GENERIC = 4,      // Y = A XA + sB B XB, explicit blocks (K columns)
+  PM_STEP_MMINUS_W = 5,  // pw = A w - B conj(w)      (Gruning step, odd half)
 };
 
 struct GenericIO {     // explicit operands for PM_GENERIC (single problem)
@@ -244,23 +266,33 @@ size_t dense_scratch_doubles(int64_t N, int nev);
 int dense_shao(const Prob* dprobs, int64_t N, int64_t Npad, bool tiles64, bool pq, int nev, double* work,
                int* dflag, double2* Z, double* lam_out, cudaStream_t s);
 
-// Krylov kernels (k_krylov.cu)
+// Krylov kernels (k_krylov.cu).  `half` selects the vectors of a Gram-Schmidt pass or a
+// normalisation: 0 the folded (or TDA) step, 1 the odd half of a Gruning step (against W
+// and the twins i V), 2 its even half and its fresh vectors (against V and the twins i W)
 template <typename ST>
 void launch_step_cgs(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t maxNpad,
-                     int ncol, int pass, cudaStream_t s);
+                     int ncol, int pass, int half, cudaStream_t s);
 template <typename ST>
 void launch_step_normalize(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t maxNpad,
-                           int start, cudaStream_t s);
+                           int start, int half, cudaStream_t s);
 template <typename ST>
 void launch_start_vector(const Prob* dprobs, int nprob, int64_t maxNpad, uint64_t seed,
                          const void* v0, cudaStream_t s);
 template <typename ST>
-void launch_restart(const Prob* dprobs, int nprob, int ph, int64_t maxNpad, int ncv,
+void launch_restart(const Prob* dprobs, int nprob, int ph, int64_t maxNpad, int ncv, bool gruning,
                     cudaStream_t s);
 
-// projected eigenproblem (k_ritz.cu)
-void launch_ritz(const Prob* dprobs, int nprob, int ncv, cudaStream_t s);
+// projected eigenproblem (k_ritz.cu); gruning: the tree of H's projection instead of the
+// folded one
+void launch_ritz(const Prob* dprobs, int nprob, int ncv, bool gruning, cudaStream_t s);
 void launch_lock_decide_form(const Prob* dprobs, int nprob, int ph, cudaStream_t s);
+// VAR_PROJECTED (k_dense.cu): the active projected problem of problem iprob as the BSE
+// matrix [[A_k, B_k], [-B_k, -A_k]] of order 2 n, solved by the dense structure-preserving
+// method; writes ritz, S and rest like launch_ritz.  n = m - k and nw = the wanted count,
+// as the host read them from the Krylov state.  Returns 0, 1 (not positive definite) or
+// -1 (CUDA error); `work` holds dense_scratch_doubles(n, nw) + projected_scratch_doubles(n, nw).
+size_t projected_scratch_doubles(int n, int nw);
+int projected_ritz(const Prob* dprobs, int iprob, int n, int nw, double* work, int* dflag, cudaStream_t s);
 
 // post-processing (k_post.cu); Z is FP64, ld 2 Npad (PH) or Npad (TDA)
 template <typename ST>

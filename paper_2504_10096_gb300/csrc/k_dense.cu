@@ -552,11 +552,12 @@ size_t dense_scratch_doubles(int64_t N, int nev) {
   return (size_t)(2 * ld * n + 4 * n + (int64_t)nev * (5 * n + n + 2 * n) + nev + 8 + 10 * 32);
 }
 
-// Dense diagonalisation of problem 0 of a PH handle: the nev lowest positive omega and
-// their right eigenvectors (unnormalised) in Z (ld 2 Npad).  Returns 0, 1 (M_r not positive
-// definite) or -1 (CUDA error).  `work` holds dense_scratch_doubles(N, nev) doubles.
-int dense_shao(const Prob* dprobs, int64_t N, int64_t Npad, bool tiles64, bool pq, int nev, double* work,
-               int* dflag, double2* Z, double* lam_out, cudaStream_t s) {
+// Steps 2-6 on an assembled M_r (step 1 is `assemble(M, ld)`): the nev lowest positive omega
+// (device, *lam_dev) and their right eigenvectors (unnormalised) in Z (ld 2 Npad).  Returns 0,
+// 1 (M_r not positive definite) or -1 (CUDA error); the stream is synchronised.
+template <typename Assemble>
+int dense_run(int64_t N, int64_t Npad, int nev, double* work, int* dflag, double2* Z, double** lam_dev,
+              Assemble assemble, cudaStream_t s) {
   const int64_t n = 2 * N;
   const int64_t ld = (n + 31) / 32 * 32;
   // sub-buffers start on 256-byte boundaries (q is read and written as double2)
@@ -576,12 +577,11 @@ int dense_shao(const Prob* dprobs, int64_t N, int64_t Npad, bool tiles64, bool p
   double* inv = take((int64_t)nev * 5 * n);   // inverse-iteration scratch, 5 n per vector
   double* Sv = take((int64_t)nev * n);
   double2* qb = reinterpret_cast<double2*>(take((int64_t)nev * 2 * n));
+  *lam_dev = lam;
   if (cudaMemsetAsync(dflag, 0, sizeof(int), s) != cudaSuccess) return -1;
   // 1.
-  count_launch();
   const dim3 g2((unsigned)((n + 31) / 32), (unsigned)((n + 7) / 8)), b2(32, 8);
-  if (tiles64) k_dn_assemble<float2><<<g2, b2, 0, s>>>(dprobs, pq ? 1 : 0, M, ld);
-  else k_dn_assemble<double2><<<g2, b2, 0, s>>>(dprobs, pq ? 1 : 0, M, ld);
+  assemble(M, ld);
   // 2. Cholesky
   for (int64_t k0 = 0; k0 < n; k0 += DNB) {
     const int kb = (int)std::min<int64_t>(DNB, n - k0);
@@ -628,12 +628,147 @@ int dense_shao(const Prob* dprobs, int64_t N, int64_t Npad, bool tiles64, bool p
   // 6.
   count_launch();
   k_dn_back<<<nev, 256, 0, s>>>(W, M, ld, n, E, T, Sv, qb, Npad, Z);
-  if (lam_out && cudaMemcpyAsync(lam_out, lam, sizeof(double) * nev, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return -1;
   int h = 0;
   if (cudaMemcpyAsync(&h, dflag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return -1;
   if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return -1;
   return h ? 1 : 0;
 }
+
+namespace {
+
+// ---------------------------------------------------------------- projected BSE variant
+// The folded recurrence builds V (M+-orthonormal) and P = M+ V, and H maps the even vectors
+// e_j = (v_j; conj(v_j)) to the odd ones o_j = (p_j; -conj(p_j)) and o_j to sum_i e_i T_ij
+// (T the projected M- M+).  In the basis x_j = e_j + o_j, y_j = e_j - o_j, which the
+// swap-and-conjugate symmetry of H maps onto each other, H's projection is the BSE matrix
+// [[A_k, B_k], [-B_k, -A_k]] of Eq. 1 with the real symmetric blocks A_k = (T + I) / 2 and
+// B_k = (I - T) / 2; its M_r (Eq. 5) is diag(I, T), positive definite.  The dense
+// structure-preserving method solves it (its omega are the singular values of T's Cholesky
+// factor, computed without squaring), and an eigenvector (a; b) is the Ritz vector
+// x a + y b = e (a + b) + o (a - b): the folded coefficients are a + b.
+
+// M_r = diag(I, T_active) of problem ip (column-major, ld); grid as k_dn_assemble
+__global__ void k_pj_assemble(const Prob* __restrict__ probs, int ip, double* __restrict__ M, int64_t ld) {
+  const Prob& p = probs[ip];
+  const KState* st = p.st;
+  const int k = st->k, l = st->l, m = st->m, h = l - k;
+  const int64_t na = m - k, n = 2 * na;
+  const int64_t i = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  const int64_t j = (int64_t)blockIdx.y * 8 + threadIdx.y;
+  if (i >= n || j >= n) return;
+  double v = 0.0;
+  if (i < na || j < na) {
+    v = i == j ? 1.0 : 0.0;
+  } else {
+    const int64_t a = i - na, b = j - na;
+    const int64_t lo = a < b ? a : b, hi = a < b ? b : a;
+    if (a == b) v = a < h ? p.theta[k + a] : p.alpha[l + (a - h)];
+    else if (hi == h && lo < h) v = p.barrow[k + lo];
+    else if (lo >= h && hi == lo + 1) v = p.beta[l + (lo - h)];
+  }
+  M[j * ld + i] = v;
+}
+
+// folded Ritz data from the small problem's eigenvectors: one CTA per wanted pair
+__global__ void __launch_bounds__(256) k_pj_coef(const Prob* __restrict__ probs, int ip, int64_t na,
+                                                 const double2* __restrict__ Zs, const double* __restrict__ lam) {
+  __shared__ double red[8];
+  __shared__ double sv[8];
+  __shared__ int si[8];
+  const Prob& p = probs[ip];
+  const KState* st = p.st;
+  const int i = blockIdx.x, tid = threadIdx.x;
+  const double2* z = Zs + (int64_t)i * 2 * na;
+  // the entry of largest modulus of c~ = a + b fixes the common phase (lowest index on ties)
+  double best = -1.0;
+  int bi = 0;
+  for (int64_t t = tid; t < na; t += 256) {
+    const double2 c = cadd(z[t], z[na + t]);
+    const double a2 = c.x * c.x + c.y * c.y;
+    if (a2 > best) { best = a2; bi = (int)t; }
+  }
+  for (int o = 16; o >= 1; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  if ((tid & 31) == 0) { sv[tid >> 5] = best; si[tid >> 5] = bi; }
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < 8; ++w)
+      if (sv[w] > sv[0] || (sv[w] == sv[0] && si[w] < si[0])) { sv[0] = sv[w]; si[0] = si[w]; }
+  }
+  __syncthreads();
+  const double2 cm = cadd(z[si[0]], z[na + si[0]]);
+  const double cmn = sqrt(cm.x * cm.x + cm.y * cm.y);
+  const double2 ph = cmn > 0.0 ? make_double2(cm.x / cmn, -cm.y / cmn) : make_double2(1.0, 0.0);  // conj phase
+  double* S = p.S + (int64_t)i * p.ncv;
+  double nr = 0.0;
+  for (int64_t t = tid; t < na; t += 256) {
+    const double2 c = cadd(z[t], z[na + t]);
+    const double v = c.x * ph.x - c.y * ph.y;   // Re(c e^{-i phi})
+    S[t] = v;
+    nr += v * v;
+  }
+  nr = block_sum(nr, red);
+  const double inv = nr > 0.0 ? 1.0 / sqrt(nr) : 0.0;
+  for (int64_t t = tid; t < na; t += 256) S[t] *= inv;
+  __syncthreads();
+  if (tid == 0) {
+    p.ritz[i] = lam[i] * lam[i];
+    p.rest[i] = fabs(p.beta[st->m - 1] * S[na - 1]);
+  }
+}
+
+__global__ void k_pj_fail(const Prob* __restrict__ probs, int ip) {
+  KState* st = probs[ip].st;
+  if (threadIdx.x == 0 && st->status == ST_OK) st->status = ST_NOTPD;
+}
+
+}  // namespace
+
+// Dense diagonalisation of problem 0 of a PH handle: the nev lowest positive omega and
+// their right eigenvectors (unnormalised) in Z (ld 2 Npad).  Returns 0, 1 (M_r not positive
+// definite) or -1 (CUDA error).  `work` holds dense_scratch_doubles(N, nev) doubles.
+int dense_shao(const Prob* dprobs, int64_t N, int64_t Npad, bool tiles64, bool pq, int nev, double* work,
+               int* dflag, double2* Z, double* lam_out, cudaStream_t s) {
+  const int64_t n = 2 * N;
+  const dim3 g2((unsigned)((n + 31) / 32), (unsigned)((n + 7) / 8)), b2(32, 8);
+  double* lam = nullptr;
+  const int rc = dense_run(N, Npad, nev, work, dflag, Z, &lam, [&](double* M, int64_t ld) {
+    count_launch();
+    if (tiles64) k_dn_assemble<float2><<<g2, b2, 0, s>>>(dprobs, pq ? 1 : 0, M, ld);
+    else k_dn_assemble<double2><<<g2, b2, 0, s>>>(dprobs, pq ? 1 : 0, M, ld);
+  }, s);
+  if (rc) return rc;
+  if (lam_out && (cudaMemcpyAsync(lam_out, lam, sizeof(double) * nev, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                  cudaStreamSynchronize(s) != cudaSuccess))
+    return -1;
+  return 0;
+}
+
+size_t projected_scratch_doubles(int n, int nw) { return (size_t)4 * n * nw + 64; }
+
+int projected_ritz(const Prob* dprobs, int iprob, int n, int nw, double* work, int* dflag, cudaStream_t s) {
+  if (n < 1 || nw < 1) return 0;
+  const int64_t n2 = 2 * (int64_t)n;
+  const dim3 g2((unsigned)((n2 + 31) / 32), (unsigned)((n2 + 7) / 8)), b2(32, 8);
+  const size_t dsz = (dense_scratch_doubles(n, nw) + 31) / 32 * 32;
+  double2* Zs = reinterpret_cast<double2*>(work + dsz);
+  double* lam = nullptr;
+  const int rc = dense_run(n, n, nw, work, dflag, Zs, &lam, [&](double* M, int64_t ld) {
+    count_launch();
+    k_pj_assemble<<<g2, b2, 0, s>>>(dprobs, iprob, M, ld);
+  }, s);
+  if (rc < 0) return rc;
+  count_launch();
+  if (rc == 1) {
+    k_pj_fail<<<1, 32, 0, s>>>(dprobs, iprob);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+  }
+  k_pj_coef<<<nw, 256, 0, s>>>(dprobs, iprob, n, Zs, lam);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 
 }  // namespace bse

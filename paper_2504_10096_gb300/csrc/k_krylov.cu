@@ -23,6 +23,26 @@
 //     w -= V Re(P^H w) + i P Im(V^H w)
 // (one extra set of Euclidean dots against V and one extra update from P,
 // no small solve).
+//
+// Gruning variant (Lanczos recurrence of H in the M inner product, M of
+// Eq. 2 positive definite, in which H = Omega M is self-adjoint).  From an
+// even start vector (u; conj(u)) the recurrence alternates between even
+// vectors (u; conj(u)) and odd ones (w; -conj(w)): H maps an even vector to
+// the odd one with top M+ u and an odd one to the even one with top M- w.
+// Only the tops are stored: V (even, M+-orthonormal, P = M+ V) and W (odd,
+// M- -orthonormal, Z = M- W); the M inner products are 2 Re(u^H M+ u') and
+// 2 Re(w^H M- w'), and H's projection is the tridiagonal with zero diagonal
+// and couplings alpha_j (u_j -> w_j) and beta_j (w_j -> u_{j+1}):
+//   odd half:  r = M+ u_j, orthogonalised against W and the twins i V,
+//              alpha_j = |r|_-, w_j = r / alpha_j, z_j = M- r / alpha_j;
+//   even half: s = z_j, orthogonalised against V and the twins i W,
+//              beta_j = |s|_+, u_{j+1} = s / beta_j, p_{j+1} = M+ s / beta_j.
+// The twins of the odd space are i V (M-(i v) = i M+ v, so i V is
+// M- -orthonormal) and <i v_c, r>_- = Im(p_c^H r); those of the even space
+// are i W with <i w_c, s>_+ = Im(z_c^H s).  In exact arithmetic both twin
+// spaces are orthogonal to the Krylov vectors (Im(P^H P) = 0 and
+// Im(V^H V) = 0 there), so each pass removes
+//   r -= W Re(Z^H r) + i V Im(P^H r),    s -= V Re(P^H s) + i W Im(Z^H s).
 #include "bse_internal.cuh"
 
 namespace bse {
@@ -49,17 +69,51 @@ __device__ __forceinline__ double2 dshfl(double2 v, int m) {
   return v;
 }
 
+// ---------------------------------------------------------------- CGS2 sets
+// The vectors of one Gram-Schmidt pass: x -= Um Re(Dm^H x) + i Ut Im(Dt^H x) on the PH
+// paths (real coefficients), x -= Um (Um^H x) on the TDA path (complex ones).  The
+// set entries are c < nm (main) and nm <= c < nm + nt (twins).  The input x of the first
+// pass of a Gruning half is a basis column (p_j, z_j); the result always goes to w.
+struct CgsSet {
+  const void* dm; const void* dt;   // dot sources
+  const void* um; const void* ut;   // update bases (the twins enter as i * Ut)
+  int nm, nt;
+};
+
+__device__ __forceinline__ CgsSet cgs_set(const Prob& p, const KState* st, int ph, int half) {
+  const int j = st->j;
+  CgsSet c;
+  if (!ph) {
+    c.dm = c.um = p.V; c.dt = c.ut = nullptr; c.nm = j + 1; c.nt = 0;
+  } else if (half == 0) {
+    c.dm = p.P; c.dt = p.V; c.um = p.V; c.ut = p.P; c.nm = c.nt = j + 1;
+  } else if (half == 1) {
+    c.dm = p.Z; c.dt = p.P; c.um = p.W; c.ut = p.V; c.nm = j; c.nt = j + 1;
+  } else {
+    c.dm = p.P; c.dt = p.Z; c.um = p.V; c.ut = p.W; c.nm = c.nt = j + 1;
+  }
+  return c;
+}
+
+// the input of the first pass of a Gruning half (a basis column), else w
+template <typename ST>
+__device__ __forceinline__ const ST* cgs_src(const Prob& p, const KState* st, int half, int pass, int newvec) {
+  if (pass == 0 && !newvec) {
+    if (half == 1) return (const ST*)p.P + (int64_t)st->j * p.Npad;
+    if (half == 2) return (const ST*)p.Z + (int64_t)st->j * p.Npad;
+  }
+  return (const ST*)p.w;
+}
+
 // ---------------------------------------------------------------- CGS2 dots
-// PH: cpart[rb][c] = sum_{rows in block rb} Re(conj(P[row, c]) w[row]) for
-// c <= j (the K-inner products with the basis) and Im(conj(V[row, c']) w[row])
-// for c = j + 1 + c' (the twin coefficients s of the header), 2 (j + 1) in
-// all; TDA: the complex conj(V[row, c]) w[row], c <= j.  grid (ceil(maxcols/2),
-// maxnrb, nprob), 8 warps: two columns per CTA, four warps per column, each
-// warp a quarter of the block rows; the four partial sums meet in shared
-// memory (fixed order).
+// PH: cpart[rb][c] = sum_{rows in block rb} Re(conj(Dm[row, c]) x[row]) for c < nm and
+// Im(conj(Dt[row, c']) x[row]) for c = nm + c' (the twin coefficients), nm + nt in all;
+// TDA: the complex conj(V[row, c]) x[row], c <= j.  grid (ceil(maxcols/2), maxnrb, nprob),
+// 8 warps: two columns per CTA, four warps per column, each warp a quarter of the block
+// rows; the four partial sums meet in shared memory (fixed order).
 template <typename ST>
 __global__ void __launch_bounds__(256)
-k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec) {
+k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec, int half, int pass) {
   using R = typename RealOf<ST>::T;
   __shared__ double2 red[2][4];
   const Prob& p = probs[blockIdx.z];
@@ -67,23 +121,23 @@ k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec) {
   if (!kphase(st, newvec)) return;
   const int rb = blockIdx.y;
   if (rb >= p.nrb) return;
-  const int j = st->j;
-  const int nset = ph ? 2 * (j + 1) : j + 1;
+  const CgsSet cs = cgs_set(p, st, ph, half);
+  const int nset = cs.nm + cs.nt;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int half = warp >> 2, quarter = warp & 3;
-  const int c = blockIdx.x * 2 + half;
+  const int hw = warp >> 2, quarter = warp & 3;
+  const int c = blockIdx.x * 2 + hw;
   if (blockIdx.x * 2 >= nset) return;                     // whole CTA
   double2 a = mk(0.0, 0.0);
   if (c < nset) {
-    const bool twin = c > j;                              // warp-uniform
-    const int col = twin ? c - (j + 1) : c;
-    const ST* Q = (const ST*)(ph && !twin ? p.P : p.V) + (int64_t)col * p.Npad;
-    const ST* w = (const ST*)p.w;
+    const bool twin = c >= cs.nm;                         // warp-uniform
+    const int col = twin ? c - cs.nm : c;
+    const ST* Q = (const ST*)(twin ? cs.dt : cs.dm) + (int64_t)col * p.Npad;
+    const ST* w = cgs_src<ST>(p, st, half, pass, newvec);
     const int64_t r0 = (int64_t)rb * ROWBLK + quarter * (ROWBLK / 4);
     const int64_t r1 = min((int64_t)p.Npad, r0 + ROWBLK / 4);
     // rounds of 8 rows per lane: all 16 loads of a round are issued before its arithmetic
     int64_t r = r0 + lane;
-    if (ph) {   // real coefficients: Re(conj(q) w), or Im(conj(v) w) = Re(conj(v) (-i w)) for twins
+    if (ph) {   // real coefficients: Re(conj(q) x), or Im(conj(q) x) = Re(conj(q) (-i x)) for twins
       R a1 = 0, a2 = 0;   // two chains (x and y products) for more ILP
       for (; r + 7 * 32 < r1; r += 8 * 32) {
         ST q[8], x[8];
@@ -136,7 +190,7 @@ k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec) {
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) a = cadd(a, dshfl(a, m));
   }
-  if (lane == 0) red[half][quarter] = a;
+  if (lane == 0) red[hw][quarter] = a;
   __syncthreads();
   if (threadIdx.x < 2) {
     const int cc = blockIdx.x * 2 + threadIdx.x;
@@ -150,15 +204,15 @@ k_cgs_dot(const Prob* __restrict__ probs, int ph, int newvec) {
 }
 
 
-// w[row] -= sum_{c <= j} V[row, c] coef[pass][c] (+ i sum_{c'} P[row, c'] coef[pass][j+1+c'] on the
-// PH path: the twin projection).  grid (ceil(maxNpad/32), nprob), 8 warps: lane = row of a
+// w[row] = x[row] - sum_{c < nm} Um[row, c] coef[pass][c] (- i sum_{c'} Ut[row, c'] coef[pass][nm+c']
+// on the PH paths: the twin projection).  grid (ceil(maxNpad/32), nprob), 8 warps: lane = row of a
 // 32-row slab, warp w takes the set entries c = w mod 8 (six or eight loads in flight each),
 // and the eight partial sums meet in shared memory.  Spreading the columns over warps keeps
 // enough loads in flight when N is only a few hundred slabs; three CTAs per SM keep N = 10^4
 // (316 slabs) in one wave (ncu: at two per SM the last 12 CTAs ran as a second wave).
 template <typename ST>
 __global__ void __launch_bounds__(256, 3)
-k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
+k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec, int half) {
   using R = typename RealOf<ST>::T;
   __shared__ ST cf[2 * MAXM + 2];
   __shared__ ST red[8][32];
@@ -167,13 +221,13 @@ k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
   if (!kphase(st, newvec)) return;
   const int64_t row = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
   if ((int64_t)blockIdx.x * 32 >= p.Npad) return;     // whole block (Npad is a multiple of 128)
-  const int j = st->j;
-  const int nj = j + 1;                     // basis columns [0, j]
-  const int nset = ph ? 2 * nj : nj;
+  const CgsSet cs = cgs_set(p, st, ph, half);
+  const int nm = cs.nm;
+  const int nset = nm + cs.nt;
   // coefficients: the row-block partial sums of the dots, added in row-block order (PH: real
   // part only); the first row slab also stores them for k_step_finish
   const double2* cp = (const double2*)p.cpart;
-  double2* coef = (double2*)p.coef + (int64_t)pass * p.ncol;
+  double2* coef = (double2*)p.coef + (int64_t)(pass & 1) * p.ncol;
   for (int c = threadIdx.x; c < nset; c += blockDim.x) {
     double2 sc = mk(0.0, 0.0);
     for (int rb = 0; rb < p.nrb; ++rb) sc = cadd(sc, cp[(int64_t)rb * p.ncol + c]);
@@ -183,14 +237,14 @@ k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const ST* vb = (const ST*)p.V + row;
-  const ST* pb = ph ? (const ST*)p.P + row : nullptr;
+  const ST* vb = (const ST*)cs.um + row;
+  const ST* pb = ph ? (const ST*)cs.ut + row : nullptr;
   constexpr int U = sizeof(ST) == 16 ? 6 : 8;   // loads in flight per thread (registers for 3 CTAs/SM)
   const int64_t ld = p.Npad;
-  // entry cc of the set: V[:, cc] for cc < nj, else the twin i P[:, cc - nj] (as (-p.y, p.x))
+  // entry cc of the set: Um[:, cc] for cc < nm, else the twin i Ut[:, cc - nm] (as (-t.y, t.x))
   auto colval = [&](int cc) -> ST {
-    if (cc < nj) return __ldg(vb + (int64_t)cc * ld);
-    const ST q = __ldg(pb + (int64_t)(cc - nj) * ld);
+    if (cc < nm) return __ldg(vb + (int64_t)cc * ld);
+    const ST q = __ldg(pb + (int64_t)(cc - nm) * ld);
     ST t;
     t.x = -q.y;
     t.y = q.x;
@@ -246,8 +300,9 @@ k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec) {
     ST tot = red[0][lane];
 #pragma unroll
     for (int q = 1; q < 8; ++q) tot = cadd(tot, red[q][lane]);
+    const ST* x = cgs_src<ST>(p, st, half, pass, newvec);
     ST* w = (ST*)p.w;
-    w[row] = csub(w[row], tot);
+    w[row] = csub(x[row], tot);
   }
 }
 
@@ -289,10 +344,23 @@ __device__ __forceinline__ double sum_norm_parts(const Prob& p) {
   return s;
 }
 
-// V[:, j+1] = w / beta, P[:, j+1] = pw / beta when beta^2 is usable.
+// Where a normalised vector goes: V[:, j+1] (and P) for the folded / TDA step and the even
+// half of a Gruning step, W[:, j] (and Z) for the odd half.
+template <typename ST>
+__device__ __forceinline__ void norm_dest(const Prob& p, const KState* st, int half, ST*& X, ST*& Y) {
+  if (half == 1) {
+    X = (ST*)p.W + (int64_t)st->j * p.Npad;
+    Y = (ST*)p.Z + (int64_t)st->j * p.Npad;
+  } else {
+    X = (ST*)p.V + (int64_t)(st->j + 1) * p.Npad;
+    Y = p.ph ? (ST*)p.P + (int64_t)(st->j + 1) * p.Npad : nullptr;
+  }
+}
+
+// X = w / beta, Y = pw / beta (norm_dest) when beta^2 is usable.
 template <typename ST>
 __global__ void __launch_bounds__(256)
-k_normalize(const Prob* __restrict__ probs, int ph, int start) {
+k_normalize(const Prob* __restrict__ probs, int ph, int start, int half) {
   using R = typename RealOf<ST>::T;
   __shared__ double sb2;
   const Prob& p = probs[blockIdx.y];
@@ -305,13 +373,10 @@ k_normalize(const Prob* __restrict__ probs, int ph, int start) {
   const R inv = (R)(1.0 / sqrt(b2));
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= p.Npad) return;
-  const int col = st->j + 1;
-  ST* V = (ST*)p.V + (int64_t)col * p.Npad;
-  V[row] = cscale(((const ST*)p.w)[row], inv);
-  if (ph) {
-    ST* P = (ST*)p.P + (int64_t)col * p.Npad;
-    P[row] = cscale(((const ST*)p.pw)[row], inv);
-  }
+  ST *X, *Y;
+  norm_dest<ST>(p, st, half, X, Y);
+  X[row] = cscale(((const ST*)p.w)[row], inv);
+  if (ph) Y[row] = cscale(((const ST*)p.pw)[row], inv);
 }
 
 // Record alpha_j, beta_j, advance j, given beta^2 = b2 of the new vector.  fresh = 0:
@@ -349,13 +414,56 @@ __device__ void step_finish_one(const Prob& p, int ph, int fresh, double b2) {
   if (st->steps >= st->maxit && !st->done) { st->done = 1; st->status = ST_NOCONV; }
 }
 
+// Gruning step: record alpha_j (odd half) or beta_j and advance j (even half), given the
+// squared M-norm b2 of the new vector; fresh = 1: a first or replacement even vector.
+// An odd vector cannot vanish when M+ is positive definite (M+ maps the j + 1 even
+// vectors onto j + 1 independent odd ones), so a vanishing alpha means not definite.
+__device__ void gk_finish_one(const Prob& p, int half, int fresh, double b2) {
+  KState* st = p.st;
+  const int j = st->j;
+  if (!isfinite(b2)) { st->status = ST_NOTFINITE; return; }
+  if (fresh) {
+    if (!(b2 > 0.0)) { st->status = ST_NOTPD; return; }
+    st->breakdown = 0;
+    st->passes += 1;
+    st->j = j + 1;
+  } else {
+    double scale = 0.0;
+    for (int i = st->k; i < st->l; ++i) scale = fmax(scale, fabs(p.theta[i]));
+    if (j > 0) scale = fmax(scale, p.beta[j - 1]);
+    if (half == 2) scale = fmax(scale, p.alpha[j]);
+    const double tiny = 1e-26 * scale * scale + 1e-300;
+    if (b2 < -1e6 * tiny) { st->status = ST_NOTPD; return; }
+    if (half == 1) {
+      if (b2 <= tiny) { st->status = ST_NOTPD; return; }
+      p.alpha[j] = sqrt(b2);
+      return;                           // the even half follows in the same step
+    }
+    st->passes += 2;
+    st->steps += 1;
+    if (b2 <= tiny) {                   // invariant subspace: the chain restarts
+      p.beta[j] = 0.0;                  // with a fresh vector (host-driven)
+      st->breakdown = 1;
+      return;
+    }
+    p.beta[j] = sqrt(b2);
+    st->j = j + 1;
+  }
+  if (st->steps >= st->maxit && !st->done) { st->done = 1; st->status = ST_NOCONV; }
+}
+
+__device__ __forceinline__ void finish_one(const Prob& p, int ph, int fresh, int half, double b2) {
+  if (half) gk_finish_one(p, half, fresh, b2);
+  else step_finish_one(p, ph, fresh, b2);
+}
+
 // One thread per problem.
-__global__ void k_step_finish(const Prob* __restrict__ probs, int nprob, int ph, int fresh) {
+__global__ void k_step_finish(const Prob* __restrict__ probs, int nprob, int ph, int fresh, int half) {
   const int ip = blockIdx.x * blockDim.x + threadIdx.x;
   if (ip >= nprob) return;
   const Prob& p = probs[ip];
   if (!kphase(p.st, fresh)) return;
-  step_finish_one(p, ph, fresh, sum_norm_parts(p));
+  finish_one(p, ph, fresh, half, sum_norm_parts(p));
 }
 
 // Problems of at most one reduction row block (Npad <= ROWBLK): the norm, the scaling of
@@ -363,7 +471,7 @@ __global__ void k_step_finish(const Prob* __restrict__ probs, int nprob, int ph,
 // three per Krylov step; the same arithmetic as k_norm_partial, k_normalize, k_step_finish).
 template <typename ST>
 __global__ void __launch_bounds__(256)
-k_norm_fused(const Prob* __restrict__ probs, int ph, int start) {
+k_norm_fused(const Prob* __restrict__ probs, int ph, int start, int half) {
   using R = typename RealOf<ST>::T;
   __shared__ double red[8];
   __shared__ double sb2;
@@ -390,16 +498,15 @@ k_norm_fused(const Prob* __restrict__ probs, int ph, int start) {
   const double b2 = sb2;
   if (b2 > 0.0 && isfinite(b2)) {
     const R inv = (R)(1.0 / sqrt(b2));
-    const int col = st->j + 1;
-    ST* V = (ST*)p.V + (int64_t)col * p.Npad;
-    ST* P = ph ? (ST*)p.P + (int64_t)col * p.Npad : nullptr;
+    ST *X, *Y;
+    norm_dest<ST>(p, st, half, X, Y);
     for (int64_t r = threadIdx.x; r < p.Npad; r += 256) {
-      V[r] = cscale(w[r], inv);
-      if (ph) P[r] = cscale(((const ST*)p.pw)[r], inv);
+      X[r] = cscale(w[r], inv);
+      if (ph) Y[r] = cscale(((const ST*)p.pw)[r], inv);
     }
   }
   __syncthreads();                     // every thread has read st->j
-  if (threadIdx.x == 0) step_finish_one(p, ph, start, b2);
+  if (threadIdx.x == 0) finish_one(p, ph, start, half, b2);
 }
 
 // ---------------------------------------------------------------- start vector
@@ -440,7 +547,8 @@ __global__ void k_start_fill(const Prob* __restrict__ probs, uint64_t seed, cons
 }
 
 // ---------------------------------------------------------------- restart
-// V2[:, i] = sum_{c < n} V[:, k0 + c] S[c, i], i < nkeep (and P2 from P).
+// V2[:, i] = sum_{c < n} V[:, k0 + c] S[c, i], i < nkeep (which = 0; P2 from P: 1; on the
+// Gruning path W2 from W and Z2 from Z with the odd-side coefficients S2: 2, 3).
 // grid (ceil(maxNpad/64), ceil(ncv/16), nprob), 256 threads: 64 rows x 16 cols,
 // each thread 1 row x 4 columns.
 template <typename ST>
@@ -458,8 +566,11 @@ k_restart_gemm(const Prob* __restrict__ probs, int which) {
   if (i0 >= nkeep) return;
   const int64_t r0 = (int64_t)blockIdx.x * 64;
   if (r0 >= p.Npad) return;
-  const ST* src = (const ST*)(which ? p.P : p.V) + (int64_t)k0 * p.Npad;
-  ST* dst = (ST*)(which ? p.P2 : p.V2);
+  const void* srcs[4] = {p.V, p.P, p.W, p.Z};
+  void* dsts[4] = {p.V2, p.P2, p.W2, p.Z2};
+  const ST* src = (const ST*)srcs[which] + (int64_t)k0 * p.Npad;
+  ST* dst = (ST*)dsts[which];
+  const double* Sc = which >= 2 ? p.S2 : p.S;
   const int tid = threadIdx.x, rr = tid & 63, cg = tid >> 6;
   ST acc[4];
 #pragma unroll
@@ -473,7 +584,7 @@ k_restart_gemm(const Prob* __restrict__ probs, int which) {
     }
     for (int e = tid; e < 32 * 16; e += 256) {
       const int cc = e >> 4, ii = e & 15;
-      ss[cc][ii] = (c0 + cc < n && i0 + ii < nkeep) ? (R)p.S[(int64_t)(i0 + ii) * p.ncv + c0 + cc] : (R)0;
+      ss[cc][ii] = (c0 + cc < n && i0 + ii < nkeep) ? (R)Sc[(int64_t)(i0 + ii) * p.ncv + c0 + cc] : (R)0;
     }
     __syncthreads();
 #pragma unroll 8
@@ -497,9 +608,10 @@ k_restart_gemm(const Prob* __restrict__ probs, int which) {
   }
 }
 
-// V[:, k0+i] = V2[:, i]; V[:, k0+nkeep] = V[:, m]; same for P.
+// V[:, k0+i] = V2[:, i]; V[:, k0+nkeep] = V[:, m]; same for P; W[:, k0+i] = W2[:, i] and
+// Z from Z2 on the Gruning path (the odd basis has no extra column).
 template <typename ST>
-__global__ void k_restart_copy(const Prob* __restrict__ probs, int ph) {
+__global__ void k_restart_copy(const Prob* __restrict__ probs, int ph, int gk) {
   const Prob& p = probs[blockIdx.y];
   const KState* st = p.st;
   if (st->status != ST_OK || !st->r_go) return;   // decided in this restart only
@@ -517,6 +629,16 @@ __global__ void k_restart_copy(const Prob* __restrict__ probs, int ph) {
     const ST pm = P[(int64_t)m * p.Npad + row];
     for (int i = 0; i < nkeep; ++i) P[(int64_t)(k0 + i) * p.Npad + row] = P2[(int64_t)i * p.Npad + row];
     P[(int64_t)(k0 + nkeep) * p.Npad + row] = pm;
+  }
+  if (gk) {
+    ST* W = (ST*)p.W;
+    ST* Z = (ST*)p.Z;
+    const ST* W2 = (const ST*)p.W2;
+    const ST* Z2 = (const ST*)p.Z2;
+    for (int i = 0; i < nkeep; ++i) {
+      W[(int64_t)(k0 + i) * p.Npad + row] = W2[(int64_t)i * p.Npad + row];
+      Z[(int64_t)(k0 + i) * p.Npad + row] = Z2[(int64_t)i * p.Npad + row];
+    }
   }
 }
 
@@ -539,28 +661,28 @@ __global__ void k_restart_commit(const Prob* __restrict__ probs, int nprob, int 
 // ---------------------------------------------------------------- launchers
 template <typename ST>
 void launch_step_cgs(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t maxNpad, int ncol,
-                     int pass, cudaStream_t s) {
+                     int pass, int half, cudaStream_t s) {
   // pass: 0/1 regular step passes; 2/3 the same for a fresh (replacement) vector
   count_launch(2);
   const int newvec = pass >= 2 ? 1 : 0;
   const int ps = pass & 1;
-  k_cgs_dot<ST><<<dim3((ncol + 1) / 2, maxnrb, nprob), 256, 0, s>>>(dprobs, ph, newvec);
-  k_cgs_update<ST><<<dim3((unsigned)((maxNpad + 31) / 32), nprob), 256, 0, s>>>(dprobs, ph, ps, newvec);
+  k_cgs_dot<ST><<<dim3((ncol + 1) / 2, maxnrb, nprob), 256, 0, s>>>(dprobs, ph, newvec, half, ps);
+  k_cgs_update<ST><<<dim3((unsigned)((maxNpad + 31) / 32), nprob), 256, 0, s>>>(dprobs, ph, ps, newvec, half);
 }
 
 template <typename ST>
 void launch_step_normalize(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t maxNpad,
-                           int start, cudaStream_t s) {
+                           int start, int half, cudaStream_t s) {
   if (maxnrb == 1) {
     count_launch();
-    k_norm_fused<ST><<<nprob, 256, 0, s>>>(dprobs, ph, start);
+    k_norm_fused<ST><<<nprob, 256, 0, s>>>(dprobs, ph, start, half);
     return;
   }
   count_launch(3);
   // start: 0 regular step, 1 fresh (first or replacement) vector
   k_norm_partial<ST><<<dim3(maxnrb, nprob), 256, 0, s>>>(dprobs, ph, start);
-  k_normalize<ST><<<dim3((unsigned)((maxNpad + 255) / 256), nprob), 256, 0, s>>>(dprobs, ph, start);
-  k_step_finish<<<(nprob + 127) / 128, 128, 0, s>>>(dprobs, nprob, ph, start);
+  k_normalize<ST><<<dim3((unsigned)((maxNpad + 255) / 256), nprob), 256, 0, s>>>(dprobs, ph, start, half);
+  k_step_finish<<<(nprob + 127) / 128, 128, 0, s>>>(dprobs, nprob, ph, start, half);
 }
 
 template <typename ST>
@@ -573,22 +695,24 @@ void launch_start_vector(const Prob* dprobs, int nprob, int64_t maxNpad, uint64_
 }
 
 template <typename ST>
-void launch_restart(const Prob* dprobs, int nprob, int ph, int64_t maxNpad, int ncv, cudaStream_t s) {
-  count_launch(ph ? 4 : 3);
+void launch_restart(const Prob* dprobs, int nprob, int ph, int64_t maxNpad, int ncv, bool gruning,
+                    cudaStream_t s) {
+  const int ngemm = ph ? (gruning ? 4 : 2) : 1;
+  count_launch(ngemm + 2);
   const unsigned gx = (unsigned)((maxNpad + 63) / 64);
-  k_restart_gemm<ST><<<dim3(gx, (ncv + 15) / 16, nprob), 256, 0, s>>>(dprobs, 0);
-  if (ph) k_restart_gemm<ST><<<dim3(gx, (ncv + 15) / 16, nprob), 256, 0, s>>>(dprobs, 1);
+  for (int which = 0; which < ngemm; ++which)
+    k_restart_gemm<ST><<<dim3(gx, (ncv + 15) / 16, nprob), 256, 0, s>>>(dprobs, which);
   const unsigned gr = (unsigned)((maxNpad + 255) / 256);
-  k_restart_copy<ST><<<dim3(gr, nprob), 256, 0, s>>>(dprobs, ph);
+  k_restart_copy<ST><<<dim3(gr, nprob), 256, 0, s>>>(dprobs, ph, gruning ? 1 : 0);
   k_restart_commit<<<(nprob + 127) / 128, 128, 0, s>>>(dprobs, nprob, ph);
 }
 
-#define INST(ST)                                                                                   \
-  template void launch_step_cgs<ST>(const Prob*, int, int, int, int64_t, int, int, cudaStream_t); \
-  template void launch_step_normalize<ST>(const Prob*, int, int, int, int64_t, int, cudaStream_t); \
-  template void launch_start_vector<ST>(const Prob*, int, int64_t, uint64_t, const void*,         \
-                                        cudaStream_t);                                             \
-  template void launch_restart<ST>(const Prob*, int, int, int64_t, int, cudaStream_t);
+#define INST(ST)                                                                                        \
+  template void launch_step_cgs<ST>(const Prob*, int, int, int, int64_t, int, int, int, cudaStream_t); \
+  template void launch_step_normalize<ST>(const Prob*, int, int, int, int64_t, int, int, cudaStream_t); \
+  template void launch_start_vector<ST>(const Prob*, int, int64_t, uint64_t, const void*,              \
+                                        cudaStream_t);                                                  \
+  template void launch_restart<ST>(const Prob*, int, int, int64_t, int, bool, cudaStream_t);
 INST(float2)
 INST(double2)
 #undef INST

@@ -5,7 +5,9 @@
 //     X = omega u + M+ u,   Y = conj(omega u - M+ u)
 // satisfy H (X; Y) = omega (X; Y); the columns are then scaled so that
 // z^H Omega z = |X|^2 - |Y|^2 = 1.  The -omega partner (conj Y; conj X) and the
-// left eigenvectors (X; -Y) follow from Eq. 7 without further work.
+// left eigenvectors (X; -Y) follow from Eq. 7 without further work.  On the
+// Gruning path the converged pair (u, w) of even and odd tops gives
+// X = u + w, Y = conj(u - w) directly (w = M+ u / omega).
 //
 // Final FP64 check: Hz from the stored blocks (Y1 = A X + B Y,
 // Y2 = -conj(A conj(Y) + B conj(X))), the Omega-Rayleigh quotient
@@ -33,6 +35,12 @@ __global__ void k_recover(const Prob* __restrict__ probs, int iprob, int ph, dou
   const double2 u = ccvt<double2>(((const ST*)p.V)[(int64_t)i * p.Npad + row]);
   double2* z = Z + (int64_t)i * ldz;
   if (!ph) { z[row] = u; return; }
+  if (p.variant == VAR_GRUNING) {   // z = even + odd vector: (u + w; conj(u - w))
+    const double2 w = ccvt<double2>(((const ST*)p.W)[(int64_t)i * p.Npad + row]);
+    z[row] = cadd(u, w);
+    z[p.Npad + row] = conjc(csub(u, w));
+    return;
+  }
   const double2 pu = ccvt<double2>(((const ST*)p.P)[(int64_t)i * p.Npad + row]);
   const double om = sqrt(p.theta[i]);
   const double2 X = mk(om * u.x + pu.x, om * u.y + pu.y);

@@ -64,6 +64,9 @@ __device__ __forceinline__ bool prod_operands(const Prob& p, int mode, const Gen
     case PM_START_MPLUS:
       if (!fresh) return false;
       x = (const ST*)p.w; y = (ST*)p.pw; sB = (R)1; return true;
+    case PM_STEP_MMINUS_W:
+      if (fresh || j >= p.ncv) return false;
+      x = (const ST*)p.w; y = (ST*)p.pw; sB = (R)-1; return true;
   }
   return false;
 }

@@ -114,6 +114,9 @@ __device__ __forceinline__ bool df_operands(const Prob& p, int mode, const Gener
     case PM_START_MPLUS:
       if (!fresh) return false;
       x = (const double2*)p.w; sB = 1.0; return true;
+    case PM_STEP_MMINUS_W:
+      if (fresh || j >= p.ncv) return false;
+      x = (const double2*)p.w; sB = -1.0; return true;
   }
   return false;
 }

@@ -14,6 +14,17 @@
 //   * (T - lambda I) x = r costs O(n): used for inverse iteration, one warp
 //     per cluster of close eigenvalues, Gram-Schmidt inside a cluster.
 // Everything is FP64.
+//
+// Gruning variant: the projected matrix is H's own, the symmetric matrix with
+// zero diagonal that couples u_j -- w_j (alpha_j) and w_j -- u_{j+1} (beta_j);
+// after a restart each kept Ritz pair (u~_i, w~_i) is coupled by sigma_i and
+// w~_i to the hub u_l by rho_i.  Rotating each kept pair to (u~ +- w~)/sqrt 2
+// gives leaves +sigma_i and -sigma_i with couplings +-rho_i / sqrt 2 to the hub,
+// followed by the path u_l, w_l, u_{l+1}, ..., w_{m-1}: the same star-plus-path
+// tree, of order 2 (m - k), whose spectrum is +-sigma.  The wanted values are
+// the indices m - k, m - k + 1, ... of its ascending spectrum (bisection as
+// above), and each eigenvector splits into even-side (V) and odd-side (W)
+// coefficients of norm 1 / sqrt 2 each.
 #include "bse_internal.cuh"
 
 namespace bse {
@@ -27,8 +38,20 @@ struct TV {        // view of the active projected matrix of one problem
   int n;           // order = h + (m - l)
 };
 
+__device__ __forceinline__ bool is_gk(const Prob& p) { return p.ph && p.variant == VAR_GRUNING; }
+
 __device__ __forceinline__ TV make_tv(const Prob& p, const KState* st) {
   TV t;
+  if (is_gk(p)) {
+    const int ld = p.jwld;
+    t.d = p.jw;
+    t.b = p.jw + ld;
+    t.h = 2 * (st->l - st->k);
+    t.a = p.jw + 2 * ld;
+    t.e = p.jw + 3 * ld;
+    t.n = 2 * (st->m - st->k);
+    return t;
+  }
   t.d = p.theta + st->k;
   t.b = p.barrow + st->k;
   t.h = st->l - st->k;
@@ -36,6 +59,37 @@ __device__ __forceinline__ TV make_tv(const Prob& p, const KState* st) {
   t.e = p.beta + st->l;
   t.n = st->m - st->k;
   return t;
+}
+
+// column i of the projected problem's Ritz vectors (the tree's, on the Gruning path)
+__device__ __forceinline__ double* ritz_vec(const Prob& p, int i) {
+  return is_gk(p) ? p.jw + 4 * (int64_t)p.jwld + (int64_t)i * p.jwld : p.S + (int64_t)i * p.ncv;
+}
+
+// Gruning path: the tree arrays of the active block (one thread per problem)
+__global__ void k_gk_form(const Prob* __restrict__ probs, int nprob) {
+  const int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= nprob) return;
+  const Prob& p = probs[ip];
+  const KState* st = p.st;
+  if (st->done || st->status != ST_OK) return;
+  const int k = st->k, l = st->l, m = st->m, h = l - k, ld = p.jwld;
+  double* d = p.jw;
+  double* b = p.jw + ld;
+  double* a = p.jw + 2 * ld;
+  double* e = p.jw + 3 * ld;
+  const double r2 = 0.70710678118654752440;
+  for (int i = 0; i < h; ++i) {
+    d[i] = p.theta[k + i];
+    d[h + i] = -p.theta[k + i];
+    b[i] = p.barrow[k + i] * r2;
+    b[h + i] = -p.barrow[k + i] * r2;
+  }
+  for (int t = 0; t < 2 * (m - l); ++t) a[t] = 0.0;
+  for (int t = 0; t < m - l; ++t) {
+    e[2 * t] = p.alpha[l + t];
+    if (t + 1 < m - l) e[2 * t + 1] = p.beta[l + t];
+  }
 }
 
 __device__ __forceinline__ int nwanted(const KState* st) {
@@ -105,6 +159,7 @@ __global__ void __launch_bounds__(32) k_ritz_values(const Prob* __restrict__ pro
   const int i = blockIdx.x;
   if (i >= nwanted(st)) return;
   const TV T = make_tv(p, st);
+  const int idx = is_gk(p) ? (st->m - st->k) + i : i;   // position in the ascending spectrum
   const int lane = threadIdx.x;
   double lo, hi, tnorm;
   gersh(T, lo, hi, tnorm, lane);
@@ -115,7 +170,7 @@ __global__ void __launch_bounds__(32) k_ritz_values(const Prob* __restrict__ pro
     if (width <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin) break;
     const double sig = lo + width * (double)(lane + 1) / 33.0;
     const int c = sturm_count(T, sig, pivmin);
-    const unsigned mask = __ballot_sync(0xffffffffu, c > i);
+    const unsigned mask = __ballot_sync(0xffffffffu, c > idx);
     if (mask == 0u) {
       lo = __shfl_sync(0xffffffffu, sig, 31);
     } else {
@@ -234,7 +289,7 @@ __global__ void __launch_bounds__(32) k_ritz_vectors(const Prob* __restrict__ pr
   if (i0 > 0 && rz[i0] - rz[i0 - 1] < ctol) return;   // not a cluster leader
   int i1 = i0 + 1;
   while (i1 < nw && rz[i1] - rz[i1 - 1] < ctol) ++i1;
-  const int M = p.ncv;
+  const int M = is_gk(p) ? p.jwld : p.ncv;    // scratch stride
   Fact F;
   F.invd = sm;
   F.dl = sm + M;
@@ -264,7 +319,7 @@ __global__ void __launch_bounds__(32) k_ritz_vectors(const Prob* __restrict__ pr
       // orthogonalise against the cluster's earlier vectors (twice), normalise
       for (int rep = 0; rep < 2; ++rep) {
         for (int c = i0; c < i; ++c) {
-          const double* sc = p.S + (int64_t)c * M;
+          const double* sc = ritz_vec(p, c);
           double dot = 0.0;
           for (int t = lane; t < n; t += 32) dot += sc[t] * x[t];
           dot = warp_sum(dot);
@@ -282,9 +337,27 @@ __global__ void __launch_bounds__(32) k_ritz_vectors(const Prob* __restrict__ pr
       if (lane == 0) solve_tree(T, F, x);
       __syncwarp();
     }
-    double* out = p.S + (int64_t)i * M;
+    double* out = ritz_vec(p, i);
     for (int t = lane; t < n; t += 32) out[t] = x[t];
-    if (lane == 0) p.rest[i] = fabs(p.beta[st->m - 1] * x[n - 1]);
+    if (is_gk(p)) {
+      // even-side (u~_k.., hub, u_{l+1}..) and odd-side (w~_k.., w_l..) coefficients, each
+      // of norm 1 after the factor sqrt 2
+      const int h = st->l - st->k, nt = st->m - st->l;
+      const double s2 = 1.41421356237309504880;
+      double* Se = p.S + (int64_t)i * p.ncv;
+      double* So = p.S2 + (int64_t)i * p.ncv;
+      for (int c = lane; c < h; c += 32) {
+        Se[c] = x[c] + x[h + c];
+        So[c] = x[c] - x[h + c];
+      }
+      for (int t = lane; t < nt; t += 32) {
+        So[h + t] = s2 * x[2 * h + 1 + 2 * t];
+        Se[h + t] = s2 * x[2 * h + 2 * t];
+      }
+      if (lane == 0) p.rest[i] = fabs(p.beta[st->m - 1] * s2 * x[n - 1]);
+    } else if (lane == 0) {
+      p.rest[i] = fabs(p.beta[st->m - 1] * x[n - 1]);
+    }
     __syncwarp();
   }
 }
@@ -313,7 +386,8 @@ __global__ void k_lock_decide(const Prob* __restrict__ probs, int nprob, int ph)
   const double bl = p.beta[m - 1];
   for (int i = 0; i < nkeep; ++i) {
     p.theta[k + i] = p.ritz[i];
-    p.barrow[k + i] = i < nl ? 0.0 : bl * p.S[(int64_t)i * p.ncv + (n - 1)];
+    const double* Sl = is_gk(p) ? p.S2 : p.S;   // the last basis vector's side
+    p.barrow[k + i] = i < nl ? 0.0 : bl * Sl[(int64_t)i * p.ncv + (n - 1)];
   }
   st->beta_last = bl;
   st->r_k0 = k;
@@ -322,10 +396,15 @@ __global__ void k_lock_decide(const Prob* __restrict__ probs, int nprob, int ph)
   st->r_go = 1;
 }
 
-void launch_ritz(const Prob* dprobs, int nprob, int ncv, cudaStream_t s) {
+void launch_ritz(const Prob* dprobs, int nprob, int ncv, bool gruning, cudaStream_t s) {
+  if (gruning) {
+    count_launch();
+    k_gk_form<<<(nprob + 127) / 128, 128, 0, s>>>(dprobs, nprob);
+  }
   count_launch(2);
   k_ritz_values<<<dim3(ncv, nprob), 32, 0, s>>>(dprobs);
-  const size_t sm = (size_t)ncv * 6 * sizeof(double) + (size_t)ncv + 16;
+  const size_t M = gruning ? (size_t)(2 * ncv + 2) : (size_t)ncv;
+  const size_t sm = M * 6 * sizeof(double) + M + 16;
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_ritz_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_ritz_vectors<<<dim3(ncv, nprob), 32, sm, s>>>(dprobs);
 }

@@ -132,3 +132,37 @@ def test_newer_entry_points_validate_without_gpu(lib):
     assert lib.bse_measure_fp64_peak(0, ctypes.byref(tf), ctypes.byref(ms)) == bse.BSE_EINVAL
     assert lib.bse_measure_fp64_peak(1 << 25, ctypes.byref(tf), ctypes.byref(ms)) == bse.BSE_EINVAL
     assert lib.bse_measure_fp64_peak(100, None, None) == bse.BSE_EINVAL
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of bse_solve_opts and bse_stats have the C layout
+    (offset of every field and the size), checked against gcc on the header."""
+    import shutil
+    import subprocess
+    from paper_2504_10096_gb300 import bse
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bse.h"', "int main(void) {"]
+    for cls in (bse.bse_solve_opts, bse.bse_stats):
+        name = cls.__name__
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            name, field, val = line.split()
+            got[(name, field)] = int(val)
+    for cls in (bse.bse_solve_opts, bse.bse_stats):
+        name = cls.__name__
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
+

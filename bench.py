@@ -7,9 +7,10 @@ ingest (packing of A and B already resident in HBM) + solve (folded
 products, CGS2, projected eigenproblem, restart/lock, recovery, FP64
 residuals).  The same JSON line carries, measured in the same run:
   * "config4": the metric's own configuration -- PH N = 50000, complex64 A
-    and B, lowest 200, residual <= 1e-6 -- solved once on the mixed path and
-    once on the plain FP64 path, with the speed-up and the mixed product's
-    bandwidth (--skip-config4 / --no-config4-fp64 leave it out or shorten it);
+    and B, lowest 200, residual <= 1e-6 -- solved once on the mixed path, with
+    the mixed product's bandwidth; --config4-fp64 adds the plain FP64 solve of
+    the same values and the speed-up (about eleven more minutes, so it is not
+    in the default run); --skip-config4 leaves the record out;
   * the block-product roofline against the FP64 FMA peak measured in the run,
     the adjoint, the e2e solve through host buffers, and the double-FP32
     variant of the headline solve.
@@ -398,6 +399,7 @@ def config4_record(args, stream):
                     "product_ms_per_pass": pass_ms, "product_share": st["ms_product"] / (tm * 1e3),
                     "product_GBs": pbytes / pass_ms / 1e6,
                     "product_hbm_frac": pbytes / pass_ms / 1e6 / peaks.get("hbm_gbs", 6800.0),
+                    "product_shape": {"ctas_per_sm": st["shape_ctas_per_sm"], "strided": st["shape_strided"]},
                     "clocks": clk.summary()}
     if args.config4_fp64:
         A64 = A.to(torch.complex128)
@@ -418,6 +420,7 @@ def config4_record(args, stream):
         out["speedup_mixed_over_fp64"] = t64 / tm
     else:
         del A, B
+        out["fp64"] = None      # leg not run (--config4-fp64 adds it)
     torch.cuda.empty_cache()
     return out
 
@@ -698,7 +701,8 @@ def run_workload(args):
             solver.close()
             out.update({f"{name}_s": t, f"{name}_steps": st["steps"], f"{name}_passes": st["passes"],
                         f"{name}_max_residual": st["max_residual"], f"{name}_nconv": int(nconv),
-                        f"{name}_product_ms_per_pass": st["ms_product"] / max(st["passes"], 1)})
+                        f"{name}_product_ms_per_pass": st["ms_product"] / max(st["passes"], 1),
+                        f"{name}_product_shape": [st["shape_ctas_per_sm"], st["shape_strided"]]})
             return vals, t
 
         # the mixed path: complex64 storage, FP64 basis, double-FP32 products
@@ -740,8 +744,8 @@ def main():
                     help="product mode: complex64 storage with the mixed path's products (BSE_C64_MIXED)")
     ap.add_argument("--skip-config4", action="store_true",
                     help="solve mode: leave out the config-4 record (mixed vs FP64 at N = 50000)")
-    ap.add_argument("--no-config4-fp64", dest="config4_fp64", action="store_false",
-                    help="solve mode: config-4 record without its plain FP64 leg")
+    ap.add_argument("--config4-fp64", dest="config4_fp64", action="store_true",
+                    help="solve mode: add the plain FP64 solve of config 4 and the mixed-over-FP64 speed-up")
     ap.add_argument("--tau", type=float, default=0.0,
                     help="product mode with --mixed: tile threshold (0: the tol-1e-6 default, <0: every tile exact)")
     ap.add_argument("--ncv", type=int, default=0, help="solve mode: Krylov subspace size (0 = library default)")

@@ -590,17 +590,28 @@ k_mx_stage_x(const Prob* __restrict__ probs, int mode, GenericIO io) {
   }
 }
 
-constexpr int MX_THREADS = 512;                       // 16 column lanes x 32 row lanes
-constexpr int MX_WARPS = MX_THREADS / 32;
-constexpr int MX_ROWS = 32;                           // rows of a slab
-constexpr int MX_SLABS = TS / MX_ROWS;                // slabs per tile
-constexpr int MX_NST = 3;                             // pipeline stages
-constexpr uint32_t MX_HALF = MX_ROWS * TS * 8;        // one matrix's slab: 32 KiB
-constexpr uint32_t MX_STAGE = 2 * MX_HALF;            // A and B: 64 KiB
-constexpr uint32_t MX_XBYTES = 2 * TS * 8;            // one staged vector chunk (hi, lo): 2 KiB
-constexpr uint32_t MX_XOFF = MX_NST * MX_STAGE;       // two x buffers of (column, row) chunks
-constexpr uint32_t MX_REDOFF = MX_XOFF + 2 * 2 * MX_XBYTES;
-constexpr uint32_t MX_SMEM = MX_REDOFF + 8 * TS * sizeof(DFC);   // + column-reduction buffer
+// Two shapes of the coarse-tile kernel (the launch-shape tuner picks one per handle by timing):
+// NT = 512 threads with 32-row slabs, one CTA per SM (216 KiB of shared memory), or NT = 256
+// with 16-row slabs, two CTAs per SM (112 KiB each), whose block barriers overlap the other
+// CTA's work.  16 column lanes x NT / 16 row lanes; the row lanes are the rows of a slab.
+template <int NT>
+struct Mx {
+  static constexpr int THREADS = NT;
+  static constexpr int CTAS = 512 / NT;                  // CTAs per SM
+  static constexpr int WARPS = NT / 32;
+  static constexpr int ROWS = NT / 16;                   // rows of a slab
+  static constexpr int SLABS = TS / ROWS;                // slabs per tile (a multiple of 4)
+  static constexpr int NST = 3;                          // pipeline stages
+  static constexpr uint32_t HALF = ROWS * TS * 8;        // one matrix's slab
+  static constexpr uint32_t STAGE = 2 * HALF;            // A and B
+  static constexpr uint32_t XBYTES = 2 * TS * 8;         // one staged vector chunk (hi, lo): 2 KiB
+  static constexpr uint32_t XOFF = NST * STAGE;          // two x buffers of (column, row) chunks
+  static constexpr uint32_t REDOFF = XOFF + 2 * 2 * XBYTES;
+  static constexpr int REDW = WARPS / 2;                 // column-reduction buffer: half the warps
+  static constexpr uint32_t SMEM = REDOFF + REDW * TS * sizeof(DFC);
+  // column chains sum 2 SLABS products per lane: |S| < 2^(k + 1 + log2(2 SLABS)), grid e below
+  static constexpr int COLHEAD = SLABS == 4 ? 6 : 7;
+};
 constexpr long long MX_SPIN = 1ll << 26;              // polls of a bounded wait
 
 __device__ __forceinline__ uint32_t mx_s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -632,16 +643,18 @@ __device__ __forceinline__ void mx_copy(uint32_t dst, const void* src, uint32_t 
 __device__ __forceinline__ f2 f2lo(float4 v) { return pk(v.x, v.y); }
 __device__ __forceinline__ f2 f2hi(float4 v) { return pk(v.z, v.w); }
 
-// Thread (tx, ty) = (tid % 16, tid / 16) takes row ty of each 32-row slab and the column
+// Thread (tx, ty) = (tid % 16, tid / 16) takes row ty of each slab and the column
 // pairs 2 tx + 32 b' (b' < 4), i.e. columns c_b = 2 tx + 32 (b / 2) + (b % 2), b < 8: one
 // 16-byte shared load brings two adjacent elements (A, B, x hi, x lo alike), and the 16 lanes
 // of a row read 256 contiguous bytes.  Stage release: each warp arrives on empty[s] when it
-// is done with stage s; the producer (thread 0) waits for all 16 before refilling it.
-__global__ void __launch_bounds__(MX_THREADS, 1)
+// is done with stage s; the producer (thread 0) waits for all warps before refilling it.
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT)
 k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs, int njobs, int mode,
                 GenericIO io, int strided, int* __restrict__ err) {
+  using C = Mx<NT>;
   extern __shared__ __align__(128) unsigned char smx[];
-  __shared__ uint64_t full[MX_NST], empty[MX_NST];
+  __shared__ uint64_t full[C::NST], empty[C::NST];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int lane = tid & 31, warp = tid >> 5;
   const int per = strided ? 1 : (njobs + gridDim.x - 1) / gridDim.x;
@@ -649,9 +662,9 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
   const int t1 = strided ? njobs : min(njobs, t0 + per);
   const int dt = strided ? gridDim.x : 1;
   if (tid == 0) {
-    for (int s = 0; s < MX_NST; ++s) {
+    for (int s = 0; s < C::NST; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mx_s32(&full[s])) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mx_s32(&empty[s])), "r"(MX_WARPS) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mx_s32(&empty[s])), "r"(C::WARPS) : "memory");
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -673,10 +686,10 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
         while (pt < t1 && !active(pt)) pt += dt;
         if (pt >= t1) return;
       }
-      const int s = (int)(issued % MX_NST);
-      if (issued >= MX_NST) {     // every warp is done with the previous use of stage s?
+      const int s = (int)(issued % C::NST);
+      if (issued >= C::NST) {     // every warp is done with the previous use of stage s?
         const uint32_t bar = mx_s32(&empty[s]);
-        const uint32_t par = (uint32_t)(((issued - MX_NST) / MX_NST) & 1);
+        const uint32_t par = (uint32_t)(((issued - C::NST) / C::NST) & 1);
         if (issued < must) {
           if (!mx_wait(bar, par)) { pok = false; return; }
         } else if (!mx_try(bar, par)) {
@@ -686,20 +699,20 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
       const TileJob jb = jobs[pt];
       const Prob& p = probs[jb.prob];
       const uint32_t bar = mx_s32(&full[s]);
-      const uint32_t st = mx_s32(smx) + (uint32_t)s * MX_STAGE;
-      const size_t off = ((size_t)jb.t * TS + (size_t)pa * MX_ROWS) * TS;
-      const uint32_t bytes = MX_STAGE + (pa == 0 ? 2 * MX_XBYTES : 0u);
+      const uint32_t st = mx_s32(smx) + (uint32_t)s * C::STAGE;
+      const size_t off = ((size_t)jb.t * TS + (size_t)pa * C::ROWS) * TS;
+      const uint32_t bytes = C::STAGE + (pa == 0 ? 2 * C::XBYTES : 0u);
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-      mx_copy(st, (const float2*)p.A + off, MX_HALF, bar);
-      mx_copy(st + MX_HALF, (const float2*)p.B + off, MX_HALF, bar);
+      mx_copy(st, (const float2*)p.A + off, C::HALF, bar);
+      mx_copy(st + C::HALF, (const float2*)p.B + off, C::HALF, bar);
       if (pa == 0) {   // the tile's two vector chunks, into the x buffer of its parity
-        const uint32_t xb = mx_s32(smx) + MX_XOFF + (uint32_t)(ptile & 1) * 2 * MX_XBYTES;
+        const uint32_t xb = mx_s32(smx) + C::XOFF + (uint32_t)(ptile & 1) * 2 * C::XBYTES;
         const float2* xs = (const float2*)p.xs;
-        mx_copy(xb, xs + (int64_t)jb.J * 2 * TS, MX_XBYTES, bar);
-        mx_copy(xb + MX_XBYTES, xs + (int64_t)jb.I * 2 * TS, MX_XBYTES, bar);
+        mx_copy(xb, xs + (int64_t)jb.J * 2 * TS, C::XBYTES, bar);
+        mx_copy(xb + C::XBYTES, xs + (int64_t)jb.I * 2 * TS, C::XBYTES, bar);
       }
       ++issued;
-      if (++pa == MX_SLABS) {
+      if (++pa == C::SLABS) {
         pa = 0;
         pt += dt;
         ++ptile;
@@ -707,7 +720,7 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
     }
   };
   if (tid == 0) produce(0);
-  DFC(*red)[TS] = reinterpret_cast<DFC(*)[TS]>(smx + MX_REDOFF);
+  DFC(*red)[TS] = reinterpret_cast<DFC(*)[TS]>(smx + C::REDOFF);
   const f2 zero = pk(0.f, 0.f);
   long long consumed = 0;
   int ctile = 0;
@@ -719,42 +732,46 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
     double sB;
     if (!df_operands(p, mode, io, x, sB)) continue;   // uniform per CTA
     const bool diag = jb.I == jb.J;
-    const float2* xcb = reinterpret_cast<const float2*>(smx + MX_XOFF + (ctile & 1) * 2 * MX_XBYTES);
+    const float2* xcb = reinterpret_cast<const float2*>(smx + C::XOFF + (ctile & 1) * 2 * C::XBYTES);
     const float4* xch = reinterpret_cast<const float4*>(xcb) + tx;          // column chunk J: hi pairs
     const float4* xcl = reinterpret_cast<const float4*>(xcb + TS) + tx;     //                 lo pairs
     const float2* xrh = xcb + 2 * TS;                                       // row chunk I: hi
     const float2* xrl = xrh + TS;                                           //              lo
     // bound m on every |U xh| of this tile (m < 2^(k+1), k its exponent); row chains sum 8
-    // such products per lane, column chains 8 (4 rows x 2), so |S| < 2^(k+4) (1 + 3 u); the
-    // grid 2^e with e = k + 6 keeps |S| below 2^(e-1) with a factor 2 to spare
+    // such products per lane, so |S| < 2^(k+4) (1 + 3 u) and the grid 2^e with e = k + 6
+    // keeps |S| below 2^(e-1) with a factor 2 to spare; column chains sum 16 (8 rows x 2):
+    // e = k + 7
     const float m = p.tmax[jb.t] * fmaxf(p.xmax[jb.I], p.xmax[jb.J]);
     const float sg = grid_sigma(m, 6);
     const f2 sg2 = pk(sg, sg);
-    // grid of the cross-lane sums: a lane's chain values are below 2^e, at most 32 of them are
-    // added, and 1.5 2^(e+5) leaves a factor 4 to spare (e = k + 6 of the chain grid)
+    const float sgc = grid_sigma(m, C::COLHEAD);
+    const f2 sgc2 = pk(sgc, sgc);
+    // grid of the cross-lane sums: at most 16 chain values are added (16 column lanes of a
+    // row, 16 row lanes of a column), each below 2^(k+7), so every partial sum stays below
+    // 2^(k+11) and 1.5 2^(k+11) leaves a factor 2 to spare
     const float gs = grid_sigma(m, 11);
     const float sgn = sB > 0.0 ? 1.f : -1.f;
     f2 cH[8], cL[8];
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
-      cH[b] = sg2;
+      cH[b] = sgc2;
       cL[b] = zero;
     }
-    DFC racc[MX_SLABS];
+    DFC racc[4];                      // this thread's rows of four consecutive slabs
 #pragma unroll
-    for (int a = 0; a < MX_SLABS; ++a) {
-      const int s = (int)(consumed % MX_NST);
+    for (int a = 0; a < C::SLABS; ++a) {
+      const int s = (int)(consumed % C::NST);
       if (tid == 0) produce(consumed + 1);     // this slab is issued before anyone waits for it
       // a wait that expires raises the error flag; the warp goes on (its reads stay inside
       // shared memory) and the CTA stops at the end of the tile
-      if (__any_sync(0xffffffffu, !mx_wait(mx_s32(&full[s]), (uint32_t)((consumed / MX_NST) & 1)))) {
+      if (__any_sync(0xffffffffu, !mx_wait(mx_s32(&full[s]), (uint32_t)((consumed / C::NST) & 1)))) {
         if (lane == 0) atomicExch(err, 1);
         ok = false;
       }
-      const float4* As = reinterpret_cast<const float4*>(smx + (size_t)s * MX_STAGE) + ty * (TS / 2) + tx;
-      const float4* Bs = As + MX_ROWS * (TS / 2);
+      const float4* As = reinterpret_cast<const float4*>(smx + (size_t)s * C::STAGE) + ty * (TS / 2) + tx;
+      const float4* Bs = As + C::ROWS * (TS / 2);
       // row entry of x_I: (y_re, y_im) and (y_im, -y_re), hi and lo
-      const float2 yh = xrh[ty + MX_ROWS * a], yl = xrl[ty + MX_ROWS * a];
+      const float2 yh = xrh[ty + C::ROWS * a], yl = xrl[ty + C::ROWS * a];
       const f2 y1h = pk(yh.x, yh.y), y1l = pk(yl.x, yl.y), y2h = pk(yh.y, -yh.x), y2l = pk(yl.y, -yl.x);
       // chain 1: (U_re x_re, V_re x_im); chain 2: (U_im x_re, V_im x_im)
       f2 H1 = sg2, L1 = zero, H2 = sg2, L2 = zero;
@@ -790,18 +807,13 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
       upk(sub2(H2, sg2), s2a, s2b);
       upk(L1, l1a, l1b);
       upk(L2, l2a, l2b);
-      regrid(__fsub_rn(s1a, s2b), __fsub_rn(l1a, l2b), gs, racc[a].rh, racc[a].rl);
-      regrid(__fadd_rn(s1b, s2a), __fadd_rn(l1b, l2a), gs, racc[a].ih, racc[a].il);
+      regrid(__fsub_rn(s1a, s2b), __fsub_rn(l1a, l2b), gs, racc[a & 3].rh, racc[a & 3].rl);
+      regrid(__fadd_rn(s1b, s2a), __fadd_rn(l1b, l2a), gs, racc[a & 3].ih, racc[a & 3].il);
       ++consumed;
-    }
-    if (__syncthreads_or(ok ? 0 : 1)) {
-      ok = false;
-      break;
-    }
-    ++ctile;
-    // ---- row sums: reduce-scatter of the 4 rows over the 16 column lanes, then the
-    // remaining pairs; lanes tx % 4 == 0 write row ty + 32 ((tx >> 3) * 2 + ((tx >> 2) & 1))
-    {
+      if ((a & 3) != 3) continue;
+      // ---- row sums of slabs a - 3 .. a: reduce-scatter of the 4 rows over the 16 column
+      // lanes, then the remaining pairs; lanes tx % 4 == 0 write row
+      // ty + 16 (a - 3 + (tx >> 3) * 2 + ((tx >> 2) & 1))
       const bool u8 = tx & 8;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
@@ -816,19 +828,24 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
       racc[0] = gadd(racc[0], dfc_shfl(racc[0], 2));
       racc[0] = gadd(racc[0], dfc_shfl(racc[0], 1));
       if ((tx & 3) == 0) {
-        const int a = (u8 ? 2 : 0) + (u4 ? 1 : 0);
+        const int as = a - 3 + (u8 ? 2 : 0) + (u4 ? 1 : 0);
         float4* part = (float4*)p.part;
-        part[((int64_t)jb.I * p.nT + jb.J) * TS + ty + MX_ROWS * a] = dfc_pack(racc[0]);
+        part[((int64_t)jb.I * p.nT + jb.J) * TS + ty + C::ROWS * as] = dfc_pack(racc[0]);
       }
     }
+    if (__syncthreads_or(ok ? 0 : 1)) {
+      ok = false;
+      break;
+    }
+    ++ctile;
     if (!diag) {
-      // ---- column sums over the 32 row lanes: the two of a warp (xor 16), then 16 warps
-      // in two rounds through an 8 x TS buffer.  Column of entry b: 2 tx + 32 (b / 2) + b % 2
+      // ---- column sums over the 16 row lanes: the two of a warp (xor 16), then 8 warps in
+      // two rounds through a 4 x TS buffer.  Column of entry b: 2 tx + 32 (b / 2) + b % 2
       DFC cacc[8];
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
         float hr, hi, lr, li;
-        upk(sub2(cH[b], sg2), hr, hi);
+        upk(sub2(cH[b], sgc2), hr, hi);
         upk(cL[b], lr, li);
         regrid(hr, lr, gs, cacc[b].rh, cacc[b].rl);
         regrid(hi, li, gs, cacc[b].ih, cacc[b].il);
@@ -841,12 +858,12 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
       }
       // lane keeps entries b = q + 4 up, q < 4
       auto col = [&](int b) { return 2 * tx + 32 * (b >> 1) + (b & 1); };
-      if (warp >= 8) {
+      if (warp >= C::REDW) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) red[warp - 8][col(q + (up ? 4 : 0))] = cacc[q];
+        for (int q = 0; q < 4; ++q) red[warp - C::REDW][col(q + (up ? 4 : 0))] = cacc[q];
       }
       __syncthreads();
-      if (warp < 8) {
+      if (warp < C::REDW) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int c = col(q + (up ? 4 : 0));
@@ -857,18 +874,18 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
       if (tid < TS) {
         DFC sum = red[0][tid];
 #pragma unroll
-        for (int w = 1; w < 8; ++w) sum = gadd(sum, red[w][tid]);
+        for (int w = 1; w < C::REDW; ++w) sum = gadd(sum, red[w][tid]);
         float4* part = (float4*)p.part;
         part[((int64_t)jb.J * p.nT + jb.I) * TS + tid] = dfc_pack(sum);
       }
-      __syncthreads();                 // red is free for the next tile
+      // red is next written after the next tile's block barrier
     }
   }
   if (tid == 0) {
     // finish the producer's work only as far as needed to leave no copy in flight
     if (!ok) pok = false;
     for (long long g = consumed; g < issued; ++g)
-      mx_wait(mx_s32(&full[g % MX_NST]), (uint32_t)((g / MX_NST) & 1));
+      mx_wait(mx_s32(&full[g % C::NST]), (uint32_t)((g / C::NST) & 1));
   }
   __syncthreads();
 }
@@ -954,7 +971,22 @@ void launch_product_df(const Prob* dprobs, const TileJob* jobs, int njobs, int n
   launch_prod_reduce_d(dprobs, nprob, maxnT, mode, io, s);
 }
 
-int product_mx_occupancy() { return 1; }   // one 512-thread CTA with 224 KiB of shared memory per SM
+int product_mx_occupancy() { return 2; }   // shapes: 1 (512 threads) or 2 (256 threads) CTAs per SM
+
+template <int NT>
+void launch_mx(const Prob* dprobs, const TileJob* coarse, int ncoarse, int mode, const GenericIO& io,
+               ProdShape shape, int* err, cudaStream_t s) {
+  using C = Mx<NT>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_prod_tiles_mx<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    cudaFuncSetAttribute(k_prod_tiles_mx<NT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    attr = true;
+  }
+  const ProdShape ms{shape.ctas_per_sm < 0 ? -1 : C::CTAS, shape.strided};
+  k_prod_tiles_mx<NT><<<product_grid(C::CTAS, ms, ncoarse), NT, C::SMEM, s>>>(dprobs, coarse, ncoarse, mode, io,
+                                                                            shape.strided, err);
+}
 
 void launch_product_mixed(const Prob* dprobs, const TileJob* fine, int nfine, const TileJob* coarse, int ncoarse,
                           int nprob, int maxnT, int mode, const GenericIO* io_host, ProdShape shape, int* err,
@@ -968,16 +1000,12 @@ void launch_product_mixed(const Prob* dprobs, const TileJob* fine, int nfine, co
         dprobs, fine, nfine, mode, io, 1);
   }
   if (ncoarse > 0) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_prod_tiles_mx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MX_SMEM);
-      attr = true;
-    }
     count_launch(2);
     k_mx_stage_x<<<dim3(maxnT, nprob), TS, 0, s>>>(dprobs, mode, io);
-    const ProdShape ms{1, shape.strided};
-    k_prod_tiles_mx<<<product_grid(1, ms, ncoarse), MX_THREADS, MX_SMEM, s>>>(dprobs, coarse, ncoarse, mode, io,
-                                                                             shape.strided, err);
+    // shape.ctas_per_sm: 1 -> the 512-thread kernel, otherwise the 256-thread one (two CTAs per
+    // SM; -1: one CTA per tile)
+    if (shape.ctas_per_sm == 1) launch_mx<512>(dprobs, coarse, ncoarse, mode, io, shape, err, s);
+    else launch_mx<256>(dprobs, coarse, ncoarse, mode, io, shape, err, s);
   }
   count_launch();
   launch_prod_reduce_d(dprobs, nprob, maxnT, mode, io, s);

@@ -480,12 +480,12 @@ def run_product(args):
     s.close()
 
 
-def _timed_solve(solver, nev, tol, stream, vectors=True, graphs=True):
+def _timed_solve(solver, nev, tol, stream, vectors=True, graphs=True, persistent=True):
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    vals, vecs, nconv = solver.solve(nev, tol=tol, vectors=vectors, graphs=graphs)
+    vals, vecs, nconv = solver.solve(nev, tol=tol, vectors=vectors, graphs=graphs, persistent=persistent)
     e1.record(stream)
     torch.cuda.synchronize()
     return vals, vecs, nconv, e0.elapsed_time(e1) / 1e3
@@ -511,16 +511,20 @@ def run_workload(args):
         A = torch.from_numpy(p["A"]).cuda()
         for _ in range(args.warmup):
             s = bse.Solver(A, stream=stream); s.solve(spec.nev, tol=1e-12); s.close()
-        ts, ts_stream = [], []
+        ts, ts_graphs, ts_stream = [], [], []
         for _ in range(max(args.steps, 5)):
-            s = bse.Solver(A, stream=stream)
+            s = bse.Solver(A, stream=stream)          # persistent steps (one launch per cycle)
             vals, _, nconv, t = _timed_solve(s, spec.nev, 1e-12, stream)
             st = s.stats(); s.close(); ts.append(t)
+            s = bse.Solver(A, stream=stream)          # the per-phase kernels replayed as CUDA graphs
+            _, _, _, t = _timed_solve(s, spec.nev, 1e-12, stream, persistent=False)
+            s.close(); ts_graphs.append(t)
             s = bse.Solver(A, stream=stream)          # the same solve with one launch per kernel
             _, _, _, t = _timed_solve(s, spec.nev, 1e-12, stream, graphs=False)
             s.close(); ts_stream.append(t)
         gold = np.loadtxt(os.path.join(ROOT, "tests", "golden", "config0_lambda.txt"))
         out.update({"workload": "TDA N=2000 complex128 nev=20 FP64", "s_per_solve": statistics.median(ts),
+                    "s_per_solve_graphs": statistics.median(ts_graphs),
                     "s_per_solve_stream_launches": statistics.median(ts_stream),
                     "max_rel_err_vs_oracle": float(np.max(np.abs(vals - gold) / np.abs(gold))),
                     "krylov_steps": st["steps"], "max_residual": st["max_residual"], "launches": st["launches"],

@@ -132,8 +132,14 @@ typedef struct bse_solve_opts {
                          to the Ritz value [tol / 4]                          */
   int stream_launches; /* 0: the Krylov steps of a restart cycle are replayed
                          as CUDA graphs of 1, 2, 4, ... steps, captured once
-                         per handle and subspace size; nonzero: every kernel
-                         is launched on the stream one by one [0]             */
+                         per handle and subspace size -- or, for a single
+                         problem of N <= 6144 on the folded (Shao) or TDA
+                         recurrence with BSE_C128 or BSE_C64, run as one
+                         persistent cooperative launch per restart cycle
+                         (phases separated by a bounded grid barrier; the
+                         same results bit for bit); 1: every kernel is
+                         launched on the stream one by one; 2: graphs, never
+                         the persistent launch [0]                            */
   double tile_tau;    /* BSE_C64_MIXED with B only: a packed tile whose bound
                          on |A + B|, |A - B| (per component) is at most
                          tile_tau times the largest tile bound of its problem

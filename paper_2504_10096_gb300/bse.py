@@ -306,7 +306,7 @@ class Solver:
         self.nev = 0
 
     def solve(self, nev, tol=None, ncv=0, maxit=0, seed=0, vectors=True, lock_tol=0.0, check=True,
-              graphs=True, v0=None, tile_tau=0.0, variant=BSE_VARIANT_SHAO):
+              graphs=True, v0=None, tile_tau=0.0, variant=BSE_VARIANT_SHAO, persistent=True):
         torch = _torch()
         if tol is None:
             tol = 1e-12 if self.dtype == BSE_C128 else 1e-6
@@ -318,8 +318,8 @@ class Solver:
             bdt = torch.complex64 if self.dtype == BSE_C64 else torch.complex128
             v0t = torch.as_tensor(v0).to(device=self.device, dtype=bdt).contiguous()
         opts = bse_solve_opts(ncv=ncv, maxit=maxit, seed=seed, v0=v0t.data_ptr() if v0t is not None else None,
-                              lock_tol=lock_tol, stream_launches=0 if graphs else 1, tile_tau=tile_tau,
-                              variant=variant)
+                              lock_tol=lock_tol, stream_launches=(0 if persistent else 2) if graphs else 1,
+                              tile_tau=tile_tau, variant=variant)
         rc, vals, nconv = bse_solve_ex(self.h, nev, tol, BSE_LOWEST, opts,
                                        ev.data_ptr() if ev is not None else None)
         if check:

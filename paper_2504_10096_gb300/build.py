@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbse.so")
 SOURCES = ["k_product.cu", "k_product_df.cu", "k_krylov.cu", "k_ritz.cu", "k_post.cu", "bse_api.cu",
-           "k_noalloc.cu", "k_adjoint_tc.cu", "k_haydock.cu", "k_peak.cu", "k_dense.cu"]
+           "k_noalloc.cu", "k_adjoint_tc.cu", "k_haydock.cu", "k_peak.cu", "k_dense.cu", "k_persist.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -33,7 +33,7 @@ def _stale(obj, src):
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src, os.path.join(CSRC, "bse_internal.cuh"),
+    deps = [src, os.path.join(CSRC, "bse_internal.cuh"), os.path.join(CSRC, "bse_phases.cuh"),
             os.path.join(HERE, "..", "include", "bse.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 

@@ -148,6 +148,10 @@ struct bse_handle {
   // projected-BSE variant's dense solves
   int variant = 0;
   int sg_variant = 0;        // variant of the captured graphs
+  // persistent steps (one cooperative launch per restart cycle) for one small problem, and
+  // the grid barrier they meet at
+  bool persist = true;
+  GridBar* gbar = nullptr;
   double* pj_work = nullptr;
   size_t pj_doubles = 0;
   int* pj_flag = nullptr;
@@ -402,10 +406,16 @@ struct Driver {
   // `steps` Krylov steps: graphs of 2^b steps for the binary digits of
   // `steps` (each replayed at most once per cycle, so every event pair of a
   // replay is read before it is recorded again), or plain launches
-  void run_steps(int steps) {
+  int run_steps(int steps) {
     if (!h->tuned) {                       // shapes still being compared: one launch at a time
       for (; steps > 0; --steps) step();
-      return;
+      return BSE_OK;
+    }
+    if (persistent_ok()) {
+      const int rc = run_steps_persistent(steps);
+      if (rc == 0) return BSE_OK;
+      if (rc != 1) return rc;
+      h->persist = false;                  // not available on this device: graphs from now on
     }
     if (h->graphs && h->sg_ncv != h->ncv) {
       drop_graphs();
@@ -425,6 +435,7 @@ struct Driver {
       steps -= n;
     }
     for (; steps > 0; --steps) step();     // only when steps >= 2^(kMaxGraphLog+1)
+    return BSE_OK;
   }
 
   void restart_seq(cudaStream_t st) {
@@ -480,6 +491,25 @@ struct Driver {
     restart_seq(h->stream);
   }
 
+  // one small problem on the folded (Shao) or TDA recurrence with the plain FP64 / FP32
+  // products: its steps run as one persistent launch per cycle
+  static constexpr int64_t kPersistMaxNpad = 6144;
+  bool persistent_ok() const {
+    return h->persist && h->count == 1 && !h->mixed && !h->df && (!h->ph || h->variant == VAR_SHAO) &&
+           h->p[0].Npad <= kPersistMaxNpad;
+  }
+
+  // 0: launched; 1: not available (the caller falls back); BSE_ECUDA/ENOMEM on errors
+  int run_steps_persistent(int steps) {
+    if (!h->gbar) {
+      const int rc = dalloc((void**)&h->gbar, sizeof(GridBar));
+      if (rc) return rc;
+    }
+    const int r = launch_steps_persist<ST, R>(h->dprobs, h->djobs, h->njobs, h->ph != 0, steps, h->gbar, h->stream);
+    if (r < 0) return BSE_ECUDA;
+    return r;
+  }
+
   void drop_graphs() {
     for (StepGraph& g : h->sg) {
       if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -504,11 +534,13 @@ struct Driver {
     CK(cudaMemcpyAsync(h->hstate.data(), h->dstate, sizeof(KState) * h->count, cudaMemcpyDeviceToHost,
                        h->stream));
     int perr = 0;
+    GridBar gb{};
     if (h->prod_err) CK(cudaMemcpyAsync(&perr, h->prod_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    if (h->gbar) CK(cudaMemcpyAsync(&gb, h->gbar, sizeof(GridBar), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     CK(cudaGetLastError());
     harvest_events();
-    return perr ? BSE_ETIMEOUT : BSE_OK;
+    return (perr || gb.err) ? BSE_ETIMEOUT : BSE_OK;
   }
 
   int iterate(uint64_t seed, const void* v0) {
@@ -539,7 +571,7 @@ struct Driver {
         continue;
       }
       if (steps > 0) {
-        run_steps(steps);
+        if ((rc = run_steps(steps))) return rc;
         continue;
       }
       if (h->ph && h->variant == VAR_PROJECTED) {
@@ -825,7 +857,8 @@ int solve_impl(bse_handle* h, int nev, double tol, const bse_solve_opts* opts, d
   const uint64_t seed = opts && opts->seed ? opts->seed : 12345ull;
   const double lock_tol = opts && opts->lock_tol > 0.0 ? opts->lock_tol : tol * 0.25;
   const void* v0 = (opts && h->count == 1) ? opts->v0 : nullptr;
-  const bool graphs = !(opts && opts->stream_launches);
+  const bool graphs = !(opts && opts->stream_launches == 1);
+  h->persist = !(opts && opts->stream_launches);     // 2: graph replay even where steps could persist
   const int variant = opts ? opts->variant : BSE_VARIANT_SHAO;
   if (variant < BSE_VARIANT_SHAO || variant > BSE_VARIANT_PROJECTED) return BSE_EINVAL;
   h->variant = h->ph ? variant : BSE_VARIANT_SHAO;
@@ -1636,6 +1669,7 @@ int bse_destroy(bse_handle* h) {
   dfree(h->post);
   dfreet(h->pj_work);
   dfreet(h->pj_flag);
+  dfreet(h->gbar);
   dfreet(h->adj_tiles);
   dfreet(h->adj_tiles128);
   dfree(h->adj_panels);

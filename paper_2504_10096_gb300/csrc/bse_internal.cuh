@@ -259,6 +259,20 @@ int launch_adjoint_tc(const double2* Z, int64_t ldz, int64_t Npad, int64_t N, in
                       const int2* tiles128, int64_t ntiles, float* panels, int* derr, float2* dA, float2* dB,
                       cudaStream_t s);
 
+// persistent Krylov steps for one small problem (k_persist.cu): up to `steps` steps of the
+// folded (ph) or TDA recurrence in one cooperative launch whose phases meet at a bounded grid
+// barrier.  Returns 0 (launched), 1 (not available: no cooperative launch; the caller uses the
+// per-phase kernels) or -1 (CUDA error).  A barrier wait that expires sets gb->err.
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+  int err;
+  int pad;
+};
+template <typename ST, typename R>
+int launch_steps_persist(const Prob* dprobs, const TileJob* jobs, int njobs, bool ph, int steps, GridBar* gb,
+                         cudaStream_t s);
+
 // dense structure-preserving diagonalisation (k_dense.cu): the nev lowest positive omega of
 // problem 0 of a PH handle and their right eigenvectors in Z (ld 2 Npad); returns 0, 1 (M_r not
 // positive definite) or -1 (CUDA error); `work` holds dense_scratch_doubles(N, nev) doubles

@@ -16,20 +16,9 @@
 // owns an output block row and reads tile (I,J) or the transpose of (J,I).
 #include <type_traits>
 
-#include "bse_internal.cuh"
+#include "bse_phases.cuh"
 
 namespace bse {
-
-template <typename R> struct Acc;
-template <> struct Acc<float> { using T = float2; };
-template <> struct Acc<double> { using T = double2; };
-
-template <typename T>
-__device__ __forceinline__ T shfl_xor_c(T v, int m) {
-  v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
-  v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
-  return v;
-}
 
 // (P, Q) = (A + B, A - B) -> (A, B)
 template <typename CT>
@@ -39,208 +28,28 @@ __device__ __forceinline__ void unpack_pq(CT& a, CT& b) {
   b.x = 0.5 * (pv.x - qv.x); b.y = 0.5 * (pv.y - qv.y);
 }
 
-// Resolve the input / output vectors of a product for problem p.
-// Returns false if the problem takes no part in this launch.
-template <typename ST, typename R>
-__device__ __forceinline__ bool prod_operands(const Prob& p, int mode, const GenericIO& io,
-                                              const ST*& x, ST*& y, R& sB) {
-  const KState* st = p.st;
-  if (mode == PM_GENERIC) {
-    x = (const ST*)io.xa; y = (ST*)io.y; sB = (R)io.sB; return true;
-  }
-  if (st->done || st->status != ST_OK) return false;
-  const int j = st->j;
-  const bool fresh = j < 0 || st->breakdown;
-  switch (mode) {
-    case PM_STEP_MMINUS:
-      if (fresh || j >= p.ncv) return false;
-      x = (const ST*)p.P + (int64_t)j * p.Npad; y = (ST*)p.w; sB = (R)-1; return true;
-    case PM_STEP_MPLUS:
-      if (fresh || j >= p.ncv) return false;
-      x = (const ST*)p.w; y = (ST*)p.pw; sB = (R)1; return true;
-    case PM_STEP_A:
-      if (fresh || j >= p.ncv) return false;
-      x = (const ST*)p.V + (int64_t)j * p.Npad; y = (ST*)p.w; sB = (R)0; return true;
-    case PM_START_MPLUS:
-      if (!fresh) return false;
-      x = (const ST*)p.w; y = (ST*)p.pw; sB = (R)1; return true;
-    case PM_STEP_MMINUS_W:
-      if (fresh || j >= p.ncv) return false;
-      x = (const ST*)p.w; y = (ST*)p.pw; sB = (R)-1; return true;
-  }
-  return false;
-}
-
 // A CTA walks the global job list either as one contiguous run or with stride
 // gridDim.x (ProdShape).  Registers allow one FP64 CTA per SM (FP64-pipe
 // bound) and two FP32 ones, so that twice as many tile loads are in flight
-// (the FP32 product is HBM-latency bound).
+// (the FP32 product is HBM-latency bound).  The arithmetic is prod_tiles_body.
 template <typename ST, typename R, bool HASB>
 __global__ void __launch_bounds__(PROD_THREADS, sizeof(R) == 4 ? 2 : 1)
 k_prod_tiles(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs, int njobs,
              int mode, GenericIO io, int strided) {
   using CT = typename Acc<R>::T;
-  // complex128 PH tiles hold P = A + B and Q = A - B; complex64 PH tiles hold A and B
-  constexpr bool PQ = HASB && std::is_same<ST, double2>::value;
   __shared__ CT xc[TS];      // column block J of x
   __shared__ CT xr[TS];      // row block I of x
   __shared__ CT red[8][TS];  // column reduction across warps
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int lane = tid & 31, warp = tid >> 5;
-  const int per = strided ? 1 : (njobs + gridDim.x - 1) / gridDim.x;
-  const int t0 = strided ? blockIdx.x : blockIdx.x * per;
-  const int t1 = strided ? njobs : min(njobs, t0 + per);
-  const int dt = strided ? gridDim.x : 1;
-  for (int t = t0; t < t1; t += dt) {
-    const TileJob jb = jobs[t];
-    const Prob& p = probs[jb.prob];
-    const ST* x; ST* yout; R sB;
-    if (!prod_operands<ST, R>(p, mode, io, x, yout, sB)) continue;   // uniform per CTA
-    const bool diag = (jb.I == jb.J);
-    __syncthreads();                       // smem of the previous tile is free
-    if (tid < TS) xc[tid] = ccvt<CT>(x[(int64_t)jb.J * TS + tid]);
-    else xr[tid - TS] = ccvt<CT>(x[(int64_t)jb.I * TS + tid - TS]);
-    __syncthreads();
-    // PH: M_s u = A u + s B conj(u) is real-linear; in (Re, Im) form its block
-    // row is [[U_re, -V_im], [U_im, V_re]] with U = A + s B, V = A - s B (the
-    // real matrix M_r of Eq. 5 for s = +1), and the transpose use of the same
-    // tile is [[U_re, U_im], [-V_im, V_re]].  That is 8 real FMAs per stored
-    // element pair instead of the 16 of A u + s B conj(u) as two complex
-    // products.  Complex128 tiles store P = A + B and Q = A - B, so U, V are
-    // P, Q (s = +1) or Q, P (s = -1); complex64 tiles keep A and B exact and
-    // form U, V in registers.
-    const bool pos = sB > (R)0;
-    const ST* At = (const ST*)(PQ && !pos ? p.B : p.A) + (int64_t)jb.t * (TS * TS);
-    const ST* Bt = HASB ? (const ST*)(PQ && !pos ? p.A : p.B) + (int64_t)jb.t * (TS * TS) : nullptr;
-    CT racc[8], cacc[8];
-#pragma unroll
-    for (int b = 0; b < 8; ++b) cacc[b] = czero<CT>();
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const int r = ty + 16 * a;
-      ST av[8], bv[8];
-#pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        av[b] = __ldg(At + r * TS + tx + 16 * b);
-        if (HASB) bv[b] = __ldg(Bt + r * TS + tx + 16 * b);
-      }
-      CT ra = czero<CT>();
-      const CT y = xr[r];
-#pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        const int c = tx + 16 * b;
-        const CT xv = xc[c];
-        if (HASB) {
-          CT u, v;
-          if constexpr (PQ) {
-            u = ccvt<CT>(av[b]);
-            v = ccvt<CT>(bv[b]);
-          } else {
-            const CT a0 = ccvt<CT>(av[b]), b0 = ccvt<CT>(bv[b]);
-            u.x = fma(sB, b0.x, a0.x); u.y = fma(sB, b0.y, a0.y);
-            v.x = fma(-sB, b0.x, a0.x); v.y = fma(-sB, b0.y, a0.y);
-          }
-          ra.x = fma(u.x, xv.x, ra.x); ra.x = fma(-v.y, xv.y, ra.x);    // (M_s x_J)_r
-          ra.y = fma(u.y, xv.x, ra.y); ra.y = fma(v.x, xv.y, ra.y);
-          if (!diag) {                                                  // (M_s^T x_I)_c
-            cacc[b].x = fma(u.x, y.x, cacc[b].x); cacc[b].x = fma(u.y, y.y, cacc[b].x);
-            cacc[b].y = fma(v.x, y.y, cacc[b].y); cacc[b].y = fma(-v.y, y.x, cacc[b].y);
-          }
-        } else {
-          const CT A = ccvt<CT>(av[b]);
-          cfma(ra, A, xv);                      // (A_IJ x_J)_r
-          if (!diag) cfmac(cacc[b], A, y);      // (A_IJ^H x_I)_c
-        }
-      }
-      racc[a] = ra;
-    }
-    // ---- row sums: reduce-scatter over the 16 tx lanes (xor 8, 4, 2, 1)
-    {
-      const bool u8 = tx & 8;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        CT send = u8 ? racc[q] : racc[q + 4];
-        CT keep = u8 ? racc[q + 4] : racc[q];
-        racc[q] = cadd(keep, shfl_xor_c(send, 8));
-      }
-      const bool u4 = tx & 4;
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        CT send = u4 ? racc[q] : racc[q + 2];
-        CT keep = u4 ? racc[q + 2] : racc[q];
-        racc[q] = cadd(keep, shfl_xor_c(send, 4));
-      }
-      const bool u2 = tx & 2;
-      {
-        CT send = u2 ? racc[0] : racc[1];
-        CT keep = u2 ? racc[1] : racc[0];
-        racc[0] = cadd(keep, shfl_xor_c(send, 2));
-      }
-      racc[0] = cadd(racc[0], shfl_xor_c(racc[0], 1));
-      if ((tx & 1) == 0) {
-        const int a = (tx >> 1) & 7;
-        const int r = ty + 16 * a;
-        CT* part = (CT*)p.part;
-        part[((int64_t)jb.I * p.nT + jb.J) * TS + r] = racc[0];
-      }
-    }
-    if (!diag) {
-      // ---- column sums: pair the two ty of a warp (xor 16), then across warps
-      const bool up = lane & 16;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        CT send = up ? cacc[q] : cacc[q + 4];
-        CT keep = up ? cacc[q + 4] : cacc[q];
-        cacc[q] = cadd(keep, shfl_xor_c(send, 16));
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) red[warp][tx + 16 * (q + (up ? 4 : 0))] = cacc[q];
-      __syncthreads();
-      if (tid < TS) {
-        CT s = red[0][tid];
-#pragma unroll
-        for (int w = 1; w < 8; ++w) s = cadd(s, red[w][tid]);
-        CT* part = (CT*)p.part;
-        part[((int64_t)jb.J * p.nT + jb.I) * TS + tid] = s;
-      }
-    }
-  }
+  prod_tiles_body<ST, R, HASB>(probs, jobs, njobs, mode, io, strided, blockIdx.x, gridDim.x, xc, xr, red);
 }
 
-// y[I*TS + r] = sum_J part[I][J][r]; grid (maxnT, nprob).
-constexpr int REDUCE_GROUPS = 8;
-
+// y[I*TS + r] = sum_J part[I][J][r]; grid (maxnT, nprob) (prod_reduce_body).
 template <typename ST, typename R>
 __global__ void __launch_bounds__(REDUCE_GROUPS * TS)
 k_prod_reduce(const Prob* __restrict__ probs, int mode, GenericIO io) {
   using CT = typename Acc<R>::T;
   __shared__ CT grp[REDUCE_GROUPS - 1][TS];
-  const Prob& p = probs[blockIdx.y];
-  const int I = blockIdx.x;
-  if (I >= p.nT) return;
-  const ST* x; ST* y; R sB;
-  if (!prod_operands<ST, R>(p, mode, io, x, y, sB)) return;
-  // REDUCE_GROUPS groups of 128 threads sum the slots J = g, g + G, ... in
-  // order; the group sums are then added in group order (fixed rounding order)
-  const int r = threadIdx.x & (TS - 1), g = threadIdx.x >> 7;
-  const CT* part = (const CT*)p.part + (int64_t)I * p.nT * TS;
-  CT acc = czero<CT>();
-  int J = g;
-  for (; J + 3 * REDUCE_GROUPS < p.nT; J += 4 * REDUCE_GROUPS) {   // four loads in flight, then the sums
-    CT v[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = part[(int64_t)(J + u * REDUCE_GROUPS) * TS + r];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) acc = cadd(acc, v[u]);
-  }
-  for (; J < p.nT; J += REDUCE_GROUPS) acc = cadd(acc, part[(int64_t)J * TS + r]);
-  if (g > 0) grp[g - 1][r] = acc;
-  __syncthreads();
-  if (g == 0) {
-#pragma unroll
-    for (int q = 0; q < REDUCE_GROUPS - 1; ++q) acc = cadd(acc, grp[q][r]);
-    y[(int64_t)I * TS + r] = ccvt<ST>(acc);
-  }
+  prod_reduce_body<ST, R>(probs, mode, io, blockIdx.x, blockIdx.y, grp);
 }
 
 // Same reduction for the double-FP32 kernels, whose slots hold (hi, lo) float

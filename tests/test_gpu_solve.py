@@ -193,15 +193,39 @@ def test_graph_replay_matches_stream_launches(form, dtype):
     tol = 1e-12 if dtype == "c128" else 1e-6
     v1, z1, _ = s.solve(12, tol=tol, graphs=False, check=False)
     st1 = s.stats()
-    v2, z2, _ = s.solve(12, tol=tol, graphs=True, check=False)
+    v2, z2, _ = s.solve(12, tol=tol, graphs=True, persistent=False, check=False)
     st2 = s.stats()
-    v3, z3, _ = s.solve(12, tol=tol, graphs=True, check=False)     # graphs reused from the cache
+    v3, z3, _ = s.solve(12, tol=tol, graphs=True, persistent=False, check=False)   # graphs from the cache
     st3 = s.stats()
     assert np.array_equal(v1, v2) and np.array_equal(v2, v3)
     assert torch.equal(z1, z2) and torch.equal(z2, z3)
     for k in ("steps", "passes", "restarts", "launches"):
         assert st1[k] == st2[k] == st3[k], k
     assert st2["ms_product"] > 0.0 and st3["ms_product"] > 0.0
+    s.close()
+
+
+@pytest.mark.parametrize("form,dtype,n", [("ph", "c128", 700), ("tda", "c128", 700), ("ph", "c64", 700),
+                                          ("tda", "c128", 2000), ("ph", "c128", 4000), ("tda", "c64", 3000)])
+def test_persistent_steps_match_per_phase_kernels(form, dtype, n):
+    """One small problem: the Krylov steps of a cycle run as one persistent cooperative
+    launch (phases at a grid barrier) and give the same bits as the per-phase kernels
+    (graphs and stream launches), with far fewer launches; N = 4000 and 3000 take the
+    multi-row-block norm path of the persistent kernel."""
+    A, B = problem(n, dtype, form=form, seed=91)
+    s = _solver(A, B if form == "ph" else None)
+    tol = 1e-12 if dtype == "c128" else 1e-6
+    v1, z1, n1 = s.solve(12, tol=tol, graphs=False, check=False)
+    st1 = s.stats()
+    v2, z2, _ = s.solve(12, tol=tol, graphs=True, persistent=True, check=False)
+    st2 = s.stats()
+    v3, z3, _ = s.solve(12, tol=tol, graphs=True, persistent=True, check=False)
+    assert n1 == 12 or dtype == "c64"
+    assert np.array_equal(v1, v2) and np.array_equal(v2, v3)
+    assert torch.equal(z1, z2) and torch.equal(z2, z3)
+    for k in ("steps", "passes", "restarts"):
+        assert st1[k] == st2[k], k
+    assert st2["launches"] < st1["launches"] / 3, (st2["launches"], st1["launches"])
     s.close()
 
 

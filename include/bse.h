@@ -193,7 +193,9 @@ const char* bse_strerror(int status);
  *   out     receives the handle
  *
  * Ownership: the library copies A and B into packed upper-triangle tiles in
- * its own device memory (about N^2 * elem_size bytes for A and B together);
+ * its own device memory (about N^2 * elem_size bytes for A and B together;
+ * BSE_C64_MIXED pseudo-Hermitian handles also keep fl(A + B) and fl(A - B)
+ * in the same layout, twice that; BSE_C128_DF keeps a split copy, three times);
  * the caller may free its buffers as soon as the call returns.  The handle
  * owns all its device memory and releases it in bse_destroy.
  * Paper: the redistribution of Sec. 2.1.2 / 2.2.2 from the application's

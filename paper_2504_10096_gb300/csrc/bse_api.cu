@@ -30,6 +30,7 @@ struct ProbHost {
   void* Ahl = nullptr;   // split tiles (BSE_C128_DF)
   void* Bhl = nullptr;
   float* tmax = nullptr;   // mixed PH path: per-tile bound on |U|, |V| (device)
+  void* UV = nullptr;      // mixed PH path: {U_re, V_re, U_im, V_im} records of the packed tiles
   std::vector<float> htmax;
   float tref = 0.f;        // the largest of them
   // solve buffers
@@ -704,7 +705,7 @@ int alloc_solve(bse_handle* h, int ncv) {
     if ((rc = dalloc(&q.pw, es * (size_t)q.Npad))) return rc;
     if ((rc = dalloc(&q.part, cs * (size_t)q.nT * q.nT * TS))) return rc;
     if (h->mixed) {
-      if ((rc = dalloc(&q.xs, 64 * (size_t)q.Npad))) return rc;
+      if ((rc = dalloc(&q.xs, sizeof(float4) * (size_t)q.Npad))) return rc;
       if ((rc = dalloc((void**)&q.xmax, sizeof(float) * (size_t)q.nT))) return rc;
     }
     if ((rc = dalloc((void**)&q.cpart, sizeof(double2) * (size_t)nrb * ncol))) return rc;
@@ -779,6 +780,7 @@ int upload_probs(bse_handle* h) {
     d.Ahl = q.Ahl;
     d.Bhl = q.Bhl;
     d.tmax = q.tmax;
+    d.UV = q.UV;
     d.xs = q.xs;
     d.xmax = q.xmax;
     d.variant = h->ph ? h->variant : VAR_SHAO;
@@ -1428,7 +1430,10 @@ int bse_create_batched(int count, const int64_t* N, const void* const* A, const 
       }
     }
     if (!rc && dtype == BSE_C64_MIXED && h->ph) {
-      if (!(rc = dalloc((void**)&q.tmax, sizeof(float) * (size_t)q.ntiles))) {
+      const int64_t nel = q.ntiles * TS * TS;
+      if (!(rc = dalloc(&q.UV, sizeof(float4) * (size_t)nel)))
+        launch_uv_pack((const float2*)q.A, (const float2*)q.B, nel, (float4*)q.UV, h->stream);
+      if (!rc && !(rc = dalloc((void**)&q.tmax, sizeof(float) * (size_t)q.ntiles))) {
         launch_tile_bound((const float2*)q.A, (const float2*)q.B, q.ntiles, q.tmax, h->stream);
         q.htmax.resize(q.ntiles);
         if (cudaMemcpyAsync(q.htmax.data(), q.tmax, sizeof(float) * q.ntiles, cudaMemcpyDeviceToHost, h->stream) !=
@@ -1659,6 +1664,7 @@ int bse_destroy(bse_handle* h) {
     dfree(q.Ahl);
     dfree(q.Bhl);
     dfreet(q.tmax);
+    dfree(q.UV);
   }
   dfreet(h->djobs_fine);
   dfreet(h->djobs_coarse);

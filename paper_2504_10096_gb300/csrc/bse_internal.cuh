@@ -130,7 +130,9 @@ struct Prob {
   // complex64 PH handles on the mixed path: per tile, an upper bound on every
   // |U|, |V| component (U, V = A +- B), indexed like the packed tiles
   const float* tmax;
-  void* xs;           // mixed PH path: the pre-split vector of a product, 2 x Npad x 32 B
+  const void* UV;     // mixed PH path: per packed element {U_re, V_re, U_im, V_im}, U = fl(A + B),
+                      // V = fl(A - B) (float4, laid out like the packed tiles)
+  void* xs;           // mixed PH path: the pre-split vector of a product, Npad x 16 B
   float* xmax;        // ... and the max |hi part| of each 128-entry chunk [nT]
   int variant;        // Variant (PH handles; TDA runs the plain Lanczos recurrence)
   // VAR_GRUNING: the odd basis W (tops of the odd vectors (w; -conj(w))), Npad x ncv,
@@ -221,6 +223,8 @@ void launch_product_mixed(const Prob* dprobs, const TileJob* fine, int nfine, co
                           int nprob, int maxnT, int mode, const GenericIO* io_host, ProdShape shape, int* err,
                           cudaStream_t s);
 int product_mx_occupancy();
+// {U_re, V_re, U_im, V_im} records of U = fl(A + B), V = fl(A - B) (k_product_df.cu)
+void launch_uv_pack(const float2* A, const float2* B, int64_t nelem, float4* uv, cudaStream_t s);
 // per-tile bound max(|A_re| + |B_re|, |A_im| + |B_im|) of complex64 tiles (k_product_df.cu)
 void launch_tile_bound(const float2* A, const float2* B, int64_t ntiles, float* out, cudaStream_t s);
 // sums the float4 (hi, lo) partial-sum slots of the double-FP32 kernels in FP64 (k_product.cu)

@@ -560,9 +560,10 @@ __device__ __forceinline__ void regrid(float S, float l, float gs, float& g, flo
   lo = __fadd_rn(l, __fsub_rn(S, g));
 }
 
-// x of every active problem, split once per product into chunks of 128 entries,
-// each {hi[128], lo[128]} of float2 (re, im) pairs (2 KiB, so one bulk copy stages a
-// chunk), and xmax[I] = max |hi| over chunk I; grid (maxnT, nprob), TS threads
+// x of every active problem, split once per product into chunks of 128 entries, one float4
+// record {hi_re, hi_im, lo_re, lo_im} per entry (2 KiB a chunk, so one bulk copy stages it),
+// with re and im exchanged in both pairs for the minus half (s = -1; see k_prod_tiles_mx),
+// and xmax[I] = max |hi| over chunk I; grid (maxnT, nprob), TS threads
 __global__ void __launch_bounds__(TS)
 k_mx_stage_x(const Prob* __restrict__ probs, int mode, GenericIO io) {
   __shared__ float sm[TS / 32];
@@ -574,9 +575,8 @@ k_mx_stage_x(const Prob* __restrict__ probs, int mode, GenericIO io) {
   if (!df_operands(p, mode, io, x, sB)) return;
   const int64_t r = (int64_t)I * TS + threadIdx.x;
   const float4 v = split_d(x[r]);          // {re_hi, im_hi, re_lo, im_lo}
-  float2* xs = (float2*)p.xs + (int64_t)I * 2 * TS;
-  xs[threadIdx.x] = make_float2(v.x, v.y);
-  xs[TS + threadIdx.x] = make_float2(v.z, v.w);
+  float4* xs = (float4*)p.xs + (int64_t)I * TS;
+  xs[threadIdx.x] = sB > 0.0 ? v : make_float4(v.y, v.x, v.w, v.z);
   float m = fmaxf(fabsf(v.x), fabsf(v.y));
 #pragma unroll
   for (int k = 16; k >= 1; k >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, k));
@@ -640,14 +640,15 @@ __device__ __forceinline__ void mx_copy(uint32_t dst, const void* src, uint32_t 
       : "memory");
 }
 
-__device__ __forceinline__ f2 f2lo(float4 v) { return pk(v.x, v.y); }
-__device__ __forceinline__ f2 f2hi(float4 v) { return pk(v.z, v.w); }
-
-// Thread (tx, ty) = (tid % 16, tid / 16) takes row ty of each slab and the column
-// pairs 2 tx + 32 b' (b' < 4), i.e. columns c_b = 2 tx + 32 (b / 2) + (b % 2), b < 8: one
-// 16-byte shared load brings two adjacent elements (A, B, x hi, x lo alike), and the 16 lanes
-// of a row read 256 contiguous bytes.  Stage release: each warp arrives on empty[s] when it
-// is done with stage s; the producer (thread 0) waits for all warps before refilling it.
+// The tiles are streamed as the records UV = {U_re, V_re, U_im, V_im} of U = fl(A + B),
+// V = fl(A - B) (Prob::UV), so that (U_re, V_re) and (U_im, V_im) are register pairs as
+// loaded.  For the minus half (s = -1) U and V trade places; instead of swapping them, x is
+// staged with re and im exchanged (k_mx_stage_x), which exchanges the two lanes of every
+// chain, and the combinations below read the lanes the other way round.
+// Thread (tx, ty) = (tid % 16, tid / 16) takes row ty of each slab and the columns
+// c_b = tx + 16 b, b < 8: one 16-byte shared load brings one record (UV and x alike), and the
+// 16 lanes of a row read 256 contiguous bytes.  Stage release: each warp arrives on empty[s]
+// when it is done with stage s; the producer (thread 0) waits for all warps before refilling.
 template <int NT>
 __global__ void __launch_bounds__(NT, 512 / NT)
 k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs, int njobs, int mode,
@@ -703,13 +704,12 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
       const size_t off = ((size_t)jb.t * TS + (size_t)pa * C::ROWS) * TS;
       const uint32_t bytes = C::STAGE + (pa == 0 ? 2 * C::XBYTES : 0u);
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-      mx_copy(st, (const float2*)p.A + off, C::HALF, bar);
-      mx_copy(st + C::HALF, (const float2*)p.B + off, C::HALF, bar);
+      mx_copy(st, (const float4*)p.UV + off, C::STAGE, bar);
       if (pa == 0) {   // the tile's two vector chunks, into the x buffer of its parity
         const uint32_t xb = mx_s32(smx) + C::XOFF + (uint32_t)(ptile & 1) * 2 * C::XBYTES;
-        const float2* xs = (const float2*)p.xs;
-        mx_copy(xb, xs + (int64_t)jb.J * 2 * TS, C::XBYTES, bar);
-        mx_copy(xb + C::XBYTES, xs + (int64_t)jb.I * 2 * TS, C::XBYTES, bar);
+        const float4* xs = (const float4*)p.xs;
+        mx_copy(xb, xs + (int64_t)jb.J * TS, C::XBYTES, bar);
+        mx_copy(xb + C::XBYTES, xs + (int64_t)jb.I * TS, C::XBYTES, bar);
       }
       ++issued;
       if (++pa == C::SLABS) {
@@ -732,11 +732,8 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
     double sB;
     if (!df_operands(p, mode, io, x, sB)) continue;   // uniform per CTA
     const bool diag = jb.I == jb.J;
-    const float2* xcb = reinterpret_cast<const float2*>(smx + C::XOFF + (ctile & 1) * 2 * C::XBYTES);
-    const float4* xch = reinterpret_cast<const float4*>(xcb) + tx;          // column chunk J: hi pairs
-    const float4* xcl = reinterpret_cast<const float4*>(xcb + TS) + tx;     //                 lo pairs
-    const float2* xrh = xcb + 2 * TS;                                       // row chunk I: hi
-    const float2* xrl = xrh + TS;                                           //              lo
+    const float4* xc4 = reinterpret_cast<const float4*>(smx + C::XOFF + (ctile & 1) * 2 * C::XBYTES) + tx;
+    const float4* xr4 = xc4 - tx + TS;                                       // row chunk I
     // bound m on every |U xh| of this tile (m < 2^(k+1), k its exponent); row chains sum 8
     // such products per lane, so |S| < 2^(k+4) (1 + 3 u) and the grid 2^e with e = k + 6
     // keeps |S| below 2^(e-1) with a factor 2 to spare; column chains sum 16 (8 rows x 2):
@@ -750,7 +747,8 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
     // row, 16 row lanes of a column), each below 2^(k+7), so every partial sum stays below
     // 2^(k+11) and 1.5 2^(k+11) leaves a factor 2 to spare
     const float gs = grid_sigma(m, 11);
-    const float sgn = sB > 0.0 ? 1.f : -1.f;
+    const bool neg = sB < 0.0;                       // minus half: chain lanes exchanged
+    const float sgn = neg ? -1.f : 1.f;
     f2 cH[8], cL[8];
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
@@ -758,8 +756,12 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
       cL[b] = zero;
     }
     DFC racc[4];                      // this thread's rows of four consecutive slabs
+    // groups of four slabs (the group loop is not unrolled: one copy of the slab code)
+#pragma unroll 1
+    for (int a0 = 0; a0 < C::SLABS; a0 += 4) {
 #pragma unroll
-    for (int a = 0; a < C::SLABS; ++a) {
+    for (int a4 = 0; a4 < 4; ++a4) {
+      const int a = a0 + a4;
       const int s = (int)(consumed % C::NST);
       if (tid == 0) produce(consumed + 1);     // this slab is issued before anyone waits for it
       // a wait that expires raises the error flag; the warp goes on (its reads stay inside
@@ -768,32 +770,24 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
         if (lane == 0) atomicExch(err, 1);
         ok = false;
       }
-      const float4* As = reinterpret_cast<const float4*>(smx + (size_t)s * C::STAGE) + ty * (TS / 2) + tx;
-      const float4* Bs = As + C::ROWS * (TS / 2);
-      // row entry of x_I: (y_re, y_im) and (y_im, -y_re), hi and lo
-      const float2 yh = xrh[ty + C::ROWS * a], yl = xrl[ty + C::ROWS * a];
-      const f2 y1h = pk(yh.x, yh.y), y1l = pk(yl.x, yl.y), y2h = pk(yh.y, -yh.x), y2l = pk(yl.y, -yl.x);
-      // chain 1: (U_re x_re, V_re x_im); chain 2: (U_im x_re, V_im x_im)
+      const float4* Us = reinterpret_cast<const float4*>(smx + (size_t)s * C::STAGE) + ty * TS + tx;
+      // row entry of x_I, staged as (y_re, y_im) (minus half: (y_im, y_re)); the column chains
+      // take y1 = that pair and y2 = s (y.1, -y.0), hi and lo
+      const float4 yv = xr4[ty + C::ROWS * a];
+      const f2 y1h = pk(yv.x, yv.y), y1l = pk(yv.z, yv.w);
+      const f2 y2h = pk(sgn * yv.y, -sgn * yv.x), y2l = pk(sgn * yv.w, -sgn * yv.z);
+      // plus half: chain 1 (U_re x_re, V_re x_im), chain 2 (U_im x_re, V_im x_im)
       f2 H1 = sg2, L1 = zero, H2 = sg2, L2 = zero;
 #pragma unroll
-      for (int bp = 0; bp < 4; ++bp) {
-        const float4 a4 = As[16 * bp], b4 = Bs[16 * bp], xh4 = xch[16 * bp], xl4 = xcl[16 * bp];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int b = 2 * bp + e;
-          const float ar = e ? a4.z : a4.x, ai = e ? a4.w : a4.y;
-          const float br = e ? b4.z : b4.x, bi = e ? b4.w : b4.y;
-          const f2 xh = e ? f2hi(xh4) : f2lo(xh4), xl = e ? f2hi(xl4) : f2lo(xl4);
-          // (U_re, V_re) and (U_im, V_im), rounded: scalar FMAs straight into the two halves
-          // of a register pair (no lane moves)
-          const f2 uvr = pk(__fmaf_rn(sgn, br, ar), __fmaf_rn(-sgn, br, ar));
-          const f2 uvi = pk(__fmaf_rn(sgn, bi, ai), __fmaf_rn(-sgn, bi, ai));
-          gacc(H1, L1, uvr, xh, xl);
-          gacc(H2, L2, uvi, xh, xl);
-          if (!diag) {
-            gacc(cH[b], cL[b], uvr, y1h, y1l);
-            gacc(cH[b], cL[b], uvi, y2h, y2l);
-          }
+      for (int b = 0; b < 8; ++b) {
+        const float4 uv = Us[16 * b], xv = xc4[16 * b];
+        const f2 uvr = pk(uv.x, uv.y), uvi = pk(uv.z, uv.w);
+        const f2 xh = pk(xv.x, xv.y), xl = pk(xv.z, xv.w);
+        gacc(H1, L1, uvr, xh, xl);
+        gacc(H2, L2, uvi, xh, xl);
+        if (!diag) {
+          gacc(cH[b], cL[b], uvr, y1h, y1l);
+          gacc(cH[b], cL[b], uvi, y2h, y2l);
         }
       }
       // stage s is no longer read by this warp
@@ -807,13 +801,20 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
       upk(sub2(H2, sg2), s2a, s2b);
       upk(L1, l1a, l1b);
       upk(L2, l2a, l2b);
-      regrid(__fsub_rn(s1a, s2b), __fsub_rn(l1a, l2b), gs, racc[a & 3].rh, racc[a & 3].rl);
-      regrid(__fadd_rn(s1b, s2a), __fadd_rn(l1b, l2a), gs, racc[a & 3].ih, racc[a & 3].il);
+      if (neg) {                     // the minus half accumulated with the chain lanes exchanged
+        float t;
+        t = s1a; s1a = s1b; s1b = t;
+        t = s2a; s2a = s2b; s2b = t;
+        t = l1a; l1a = l1b; l1b = t;
+        t = l2a; l2a = l2b; l2b = t;
+      }
+      regrid(__fsub_rn(s1a, s2b), __fsub_rn(l1a, l2b), gs, racc[a4].rh, racc[a4].rl);
+      regrid(__fadd_rn(s1b, s2a), __fadd_rn(l1b, l2a), gs, racc[a4].ih, racc[a4].il);
       ++consumed;
-      if ((a & 3) != 3) continue;
-      // ---- row sums of slabs a - 3 .. a: reduce-scatter of the 4 rows over the 16 column
+    }
+      // ---- row sums of slabs a0 .. a0 + 3: reduce-scatter of the 4 rows over the 16 column
       // lanes, then the remaining pairs; lanes tx % 4 == 0 write row
-      // ty + 16 (a - 3 + (tx >> 3) * 2 + ((tx >> 2) & 1))
+      // ty + ROWS (a0 + (tx >> 3) * 2 + ((tx >> 2) & 1))
       const bool u8 = tx & 8;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
@@ -828,7 +829,7 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
       racc[0] = gadd(racc[0], dfc_shfl(racc[0], 2));
       racc[0] = gadd(racc[0], dfc_shfl(racc[0], 1));
       if ((tx & 3) == 0) {
-        const int as = a - 3 + (u8 ? 2 : 0) + (u4 ? 1 : 0);
+        const int as = a0 + (u8 ? 2 : 0) + (u4 ? 1 : 0);
         float4* part = (float4*)p.part;
         part[((int64_t)jb.I * p.nT + jb.J) * TS + ty + C::ROWS * as] = dfc_pack(racc[0]);
       }
@@ -840,13 +841,19 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
     ++ctile;
     if (!diag) {
       // ---- column sums over the 16 row lanes: the two of a warp (xor 16), then 8 warps in
-      // two rounds through a 4 x TS buffer.  Column of entry b: 2 tx + 32 (b / 2) + b % 2
+      // two rounds through a REDW x TS buffer.  Column of entry b: tx + 16 b; the minus half
+      // holds (im, re) in the chain lanes
       DFC cacc[8];
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
         float hr, hi, lr, li;
         upk(sub2(cH[b], sgc2), hr, hi);
         upk(cL[b], lr, li);
+        if (neg) {
+          float t;
+          t = hr; hr = hi; hi = t;
+          t = lr; lr = li; li = t;
+        }
         regrid(hr, lr, gs, cacc[b].rh, cacc[b].rl);
         regrid(hi, li, gs, cacc[b].ih, cacc[b].il);
       }
@@ -857,7 +864,7 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
         cacc[q] = gadd(kp, dfc_shfl(snd, 16));
       }
       // lane keeps entries b = q + 4 up, q < 4
-      auto col = [&](int b) { return 2 * tx + 32 * (b >> 1) + (b & 1); };
+      auto col = [&](int b) { return tx + 16 * b; };
       if (warp >= C::REDW) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) red[warp - C::REDW][col(q + (up ? 4 : 0))] = cacc[q];
@@ -888,6 +895,16 @@ k_prod_tiles_mx(const Prob* __restrict__ probs, const TileJob* __restrict__ jobs
       mx_wait(mx_s32(&full[g % C::NST]), (uint32_t)((g / C::NST) & 1));
   }
   __syncthreads();
+}
+
+// records {U_re, V_re, U_im, V_im} of U = fl(A + B), V = fl(A - B) for every packed element
+// (the values the coarse-tile kernel multiplies, rounded once at ingest)
+__global__ void k_uv_pack(const float2* __restrict__ A, const float2* __restrict__ B, int64_t n,
+                          float4* __restrict__ uv) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 a = A[i], b = B[i];
+    uv[i] = make_float4(__fadd_rn(a.x, b.x), __fsub_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fsub_rn(a.y, b.y));
+  }
 }
 
 // per-tile bound max over the tile of max(|A_re| + |B_re|, |A_im| + |B_im|)
@@ -1015,6 +1032,11 @@ void launch_tile_bound(const float2* A, const float2* B, int64_t ntiles, float* 
   count_launch();
   const int grid = (int)std::min<int64_t>(ntiles, 4096);
   k_tile_bound<<<grid, 256, 0, s>>>(A, B, ntiles, out);
+}
+
+void launch_uv_pack(const float2* A, const float2* B, int64_t nelem, float4* uv, cudaStream_t s) {
+  count_launch();
+  k_uv_pack<<<1024, 256, 0, s>>>(A, B, nelem, uv);
 }
 
 void launch_split_tiles(const double2* packed, int64_t nelem, float4* split, cudaStream_t s) {

@@ -189,7 +189,7 @@ def _config(ncv=0):
 # ------------------------------------------------------------------ GPU arm
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_prod_tiles(+_df) launch at N = 8000
 # (profiles/k_prod_tiles_*_n8000.md); None until the current kernel has been captured
-TRAFFIC_N8000 = {"fp64": 1.057898e9 + 10.356224e6, "df": 1.067138e9 + 22.040064e6}
+TRAFFIC_N8000 = {"fp64": 1.057860e9 + 10.361088e6, "df": 1.067138e9 + 22.040064e6}
 
 
 def run_gpu(args):

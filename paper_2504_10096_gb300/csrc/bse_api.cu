@@ -442,7 +442,7 @@ struct Driver {
   void restart_seq(cudaStream_t st) {
     launch_ritz(h->dprobs, h->count, h->ncv, gruning(), st);
     launch_lock_decide_form(h->dprobs, h->count, h->ph, st);
-    launch_restart<ST>(h->dprobs, h->count, h->ph, h->maxNpad, h->ncv, gruning(), st);
+    launch_restart<ST>(h->dprobs, h->count, h->ph, h->maxNpad, h->ncv, gruning(), h->mixed, st);
   }
 
   // projected-BSE variant: each active problem's projected matrix goes through the dense
@@ -458,7 +458,7 @@ struct Driver {
       if (rc < 0) return BSE_ECUDA;
     }
     launch_lock_decide_form(h->dprobs, h->count, h->ph, h->stream);
-    launch_restart<ST>(h->dprobs, h->count, h->ph, h->maxNpad, h->ncv, false, h->stream);
+    launch_restart<ST>(h->dprobs, h->count, h->ph, h->maxNpad, h->ncv, false, h->mixed, h->stream);
     CK(cudaGetLastError());
     return BSE_OK;
   }

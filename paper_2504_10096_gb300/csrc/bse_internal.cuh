@@ -83,6 +83,7 @@ struct KState {
   long long steps, passes, restarts, maxit;
   double tol, lock_tol;
   double beta_last;   // beta_{m-1}: coupling of the last vector to V[:, m]
+  double theta_scale; // max |theta| over the kept vectors [k, l) (scale of the breakdown test)
 };
 
 // Structure-preserving Lanczos variants of the pseudo-Hermitian iteration
@@ -284,7 +285,8 @@ size_t dense_scratch_doubles(int64_t N, int nev);
 int dense_shao(const Prob* dprobs, int64_t N, int64_t Npad, bool tiles64, bool pq, int nev, double* work,
                int* dflag, double2* Z, double* lam_out, cudaStream_t s);
 
-// Krylov kernels (k_krylov.cu).  `half` selects the vectors of a Gram-Schmidt pass or a
+// Krylov kernels (k_krylov.cu); launch_restart's df: the restart GEMM of an FP64 basis in
+// double-FP32 arithmetic (the mixed path).  `half` selects the vectors of a Gram-Schmidt pass or a
 // normalisation: 0 the folded (or TDA) step, 1 the odd half of a Gruning step (against W
 // and the twins i V), 2 its even half and its fresh vectors (against V and the twins i W)
 template <typename ST>
@@ -297,7 +299,7 @@ template <typename ST>
 void launch_start_vector(const Prob* dprobs, int nprob, int64_t maxNpad, uint64_t seed,
                          const void* v0, cudaStream_t s);
 template <typename ST>
-void launch_restart(const Prob* dprobs, int nprob, int ph, int64_t maxNpad, int ncv, bool gruning,
+void launch_restart(const Prob* dprobs, int nprob, int ph, int64_t maxNpad, int ncv, bool gruning, bool df,
                     cudaStream_t s);
 
 // projected eigenproblem (k_ritz.cu); gruning: the tree of H's projection instead of the

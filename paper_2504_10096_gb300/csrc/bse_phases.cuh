@@ -431,7 +431,15 @@ __device__ __forceinline__ void cgs_update_body(const Prob* __restrict__ probs, 
   double2* coef = (double2*)p.coef + (int64_t)(pass & 1) * p.ncol;
   for (int c = threadIdx.x; c < nset; c += blockDim.x) {
     double2 sc = mk(0.0, 0.0);
-    for (int rb = 0; rb < p.nrb; ++rb) sc = cadd(sc, ldp<COH>(cp + (int64_t)rb * p.ncol + c));
+    int rb = 0;
+    for (; rb + 8 <= p.nrb; rb += 8) {      // eight loads in flight, then the sums in order
+      double2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = ldp<COH>(cp + (int64_t)(rb + u) * p.ncol + c);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) sc = cadd(sc, v[u]);
+    }
+    for (; rb < p.nrb; ++rb) sc = cadd(sc, ldp<COH>(cp + (int64_t)rb * p.ncol + c));
     if (ph) sc.y = 0.0;
     cf[c] = ccvt<ST>(sc);
     if (bx == 0) coef[c] = sc;
@@ -595,7 +603,7 @@ __device__ __forceinline__ void step_finish_one(const Prob& p, int ph, int fresh
     st->steps += 1;
     // scale of the projected matrix for the breakdown test
     double scale = fabs(a);
-    for (int i = st->k; i < st->l; ++i) scale = fmax(scale, fabs(p.theta[i]));
+    scale = fmax(scale, st->theta_scale);   // max |theta| of the kept Ritz values
     if (j > 0) scale = fmax(scale, fabs(p.beta[j - 1]));
     const double tiny = 1e-26 * scale * scale + 1e-300;
     if (ph && b2 < -1e6 * tiny) { st->status = ST_NOTPD; return; }
@@ -631,7 +639,7 @@ __device__ __forceinline__ void gk_finish_one(const Prob& p, int half, int fresh
     st->j = j + 1;
   } else {
     double scale = 0.0;
-    for (int i = st->k; i < st->l; ++i) scale = fmax(scale, fabs(p.theta[i]));
+    scale = fmax(scale, st->theta_scale);   // max |theta| of the kept Ritz values
     if (j > 0) scale = fmax(scale, p.beta[j - 1]);
     if (half == 2) scale = fmax(scale, p.alpha[j]);
     const double tiny = 1e-26 * scale * scale + 1e-300;

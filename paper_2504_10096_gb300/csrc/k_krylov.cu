@@ -196,6 +196,83 @@ k_restart_gemm(const Prob* __restrict__ probs, int which) {
   }
 }
 
+// The same product for an FP64 basis in double-FP32 arithmetic (the mixed path, whose basis and
+// coefficients need far less than FP64's 2^-53): V and S are split into FP32 (hi, lo) pairs once
+// when staged, each term v s is formed as hi*hi exactly (its FMA residual) plus the two cross
+// terms, and the sums are kept as (hi, lo) pairs with Knuth's TwoSum, about 2^-44 relative per
+// term; the FP32 pipes run this about five times faster than GB300's FP64 pipe runs the FP64 FMAs.
+__device__ __forceinline__ void df_acc(float& ah, float& al, float vh, float vl, float sh, float sl) {
+  const float pr = vh * sh;
+  const float e = __fmaf_rn(vh, sh, -pr);
+  const float t = __fmaf_rn(vh, sl, __fmaf_rn(vl, sh, e));
+  const float su = ah + pr;
+  const float bb = su - ah;
+  const float err = (ah - (su - bb)) + (pr - bb);
+  ah = su;
+  al += err + t;
+}
+
+__global__ void __launch_bounds__(256)
+k_restart_gemm_df(const Prob* __restrict__ probs, int which) {
+  __shared__ float4 sv[32][64];      // {re_hi, im_hi, re_lo, im_lo}
+  __shared__ float2 ss[32][16];      // {hi, lo}
+  const Prob& p = probs[blockIdx.z];
+  const KState* st = p.st;
+  if (st->status != ST_OK || !st->r_go) return;   // decided in this restart only
+  const int k0 = st->r_k0, nkeep = st->r_nkeep;
+  const int n = st->m - k0;
+  const int i0 = blockIdx.y * 16;
+  if (i0 >= nkeep) return;
+  const int64_t r0 = (int64_t)blockIdx.x * 64;
+  if (r0 >= p.Npad) return;
+  const void* srcs[4] = {p.V, p.P, p.W, p.Z};
+  void* dsts[4] = {p.V2, p.P2, p.W2, p.Z2};
+  const double2* src = (const double2*)srcs[which] + (int64_t)k0 * p.Npad;
+  double2* dst = (double2*)dsts[which];
+  const double* Sc = which >= 2 ? p.S2 : p.S;
+  const int tid = threadIdx.x, rr = tid & 63, cg = tid >> 6;
+  float ah[4][2], al[4][2];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) ah[q][0] = ah[q][1] = al[q][0] = al[q][1] = 0.f;
+  for (int c0 = 0; c0 < n; c0 += 32) {
+    __syncthreads();
+    for (int e = tid; e < 32 * 64; e += 256) {
+      const int cc = e >> 6, r = e & 63;
+      const int64_t row = r0 + r;
+      const double2 v = (c0 + cc < n && row < p.Npad) ? src[(int64_t)(c0 + cc) * p.Npad + row] : czero<double2>();
+      const float xh = __double2float_rn(v.x), yh = __double2float_rn(v.y);
+      sv[cc][r] = make_float4(xh, yh, __double2float_rn(v.x - (double)xh), __double2float_rn(v.y - (double)yh));
+    }
+    for (int e = tid; e < 32 * 16; e += 256) {
+      const int cc = e >> 4, ii = e & 15;
+      const double f = (c0 + cc < n && i0 + ii < nkeep) ? Sc[(int64_t)(i0 + ii) * p.ncv + c0 + cc] : 0.0;
+      const float fh = __double2float_rn(f);
+      ss[cc][ii] = make_float2(fh, __double2float_rn(f - (double)fh));
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int cc = 0; cc < 32; ++cc) {
+      const float4 v = sv[cc][rr];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 f = ss[cc][cg * 4 + q];
+        df_acc(ah[q][0], al[q][0], v.x, v.z, f.x, f.y);
+        df_acc(ah[q][1], al[q][1], v.y, v.w, f.x, f.y);
+      }
+    }
+  }
+  const int64_t row = r0 + rr;
+  if (row < p.Npad) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = i0 + cg * 4 + q;
+      if (i < nkeep)
+        dst[(int64_t)i * p.Npad + row] =
+            make_double2((double)ah[q][0] + (double)al[q][0], (double)ah[q][1] + (double)al[q][1]);
+    }
+  }
+}
+
 // V[:, k0+i] = V2[:, i]; V[:, k0+nkeep] = V[:, m]; same for P; W[:, k0+i] = W2[:, i] and
 // Z from Z2 on the Gruning path (the odd basis has no extra column).
 template <typename ST>
@@ -239,6 +316,9 @@ __global__ void k_restart_commit(const Prob* __restrict__ probs, int nprob, int 
   const int k0 = st->r_k0;
   st->k = k0 + st->r_nl;
   st->l = k0 + st->r_nkeep;
+  double ts = 0.0;
+  for (int i = st->k; i < st->l; ++i) ts = fmax(ts, fabs(p.theta[i]));
+  st->theta_scale = ts;
   st->j = st->l;
   st->restarts += 1;
   st->r_go = 0;
@@ -283,13 +363,17 @@ void launch_start_vector(const Prob* dprobs, int nprob, int64_t maxNpad, uint64_
 }
 
 template <typename ST>
-void launch_restart(const Prob* dprobs, int nprob, int ph, int64_t maxNpad, int ncv, bool gruning,
+void launch_restart(const Prob* dprobs, int nprob, int ph, int64_t maxNpad, int ncv, bool gruning, bool df,
                     cudaStream_t s) {
   const int ngemm = ph ? (gruning ? 4 : 2) : 1;
   count_launch(ngemm + 2);
   const unsigned gx = (unsigned)((maxNpad + 63) / 64);
-  for (int which = 0; which < ngemm; ++which)
-    k_restart_gemm<ST><<<dim3(gx, (ncv + 15) / 16, nprob), 256, 0, s>>>(dprobs, which);
+  for (int which = 0; which < ngemm; ++which) {
+    if (df && std::is_same<ST, double2>::value)
+      k_restart_gemm_df<<<dim3(gx, (ncv + 15) / 16, nprob), 256, 0, s>>>(dprobs, which);
+    else
+      k_restart_gemm<ST><<<dim3(gx, (ncv + 15) / 16, nprob), 256, 0, s>>>(dprobs, which);
+  }
   const unsigned gr = (unsigned)((maxNpad + 255) / 256);
   k_restart_copy<ST><<<dim3(gr, nprob), 256, 0, s>>>(dprobs, ph, gruning ? 1 : 0);
   k_restart_commit<<<(nprob + 127) / 128, 128, 0, s>>>(dprobs, nprob, ph);
@@ -300,7 +384,7 @@ void launch_restart(const Prob* dprobs, int nprob, int ph, int64_t maxNpad, int 
   template void launch_step_normalize<ST>(const Prob*, int, int, int, int64_t, int, int, cudaStream_t); \
   template void launch_start_vector<ST>(const Prob*, int, int64_t, uint64_t, const void*,              \
                                         cudaStream_t);                                                  \
-  template void launch_restart<ST>(const Prob*, int, int, int64_t, int, bool, cudaStream_t);
+  template void launch_restart<ST>(const Prob*, int, int, int64_t, int, bool, bool, cudaStream_t);
 INST(float2)
 INST(double2)
 #undef INST

@@ -44,6 +44,8 @@ struct ProbHost {
   // odd-side Ritz coefficients (allocated by the first solve that asks for the variant)
   void *W = nullptr, *Z2 = nullptr, *Zo = nullptr, *W2 = nullptr;
   double *jw = nullptr, *S2 = nullptr;
+  // mixed PH path: double-FP32 shadows of V, P and w for the Gram-Schmidt passes
+  float4 *Vs = nullptr, *Ps = nullptr, *ws = nullptr;
   // results
   double2* Z = nullptr;
   int zcols = 0;
@@ -195,6 +197,7 @@ void free_solve_buffers(ProbHost& q) {
   dfreet(q.xmax);
   dfreet(q.cpart); dfreet(q.coef); dfreet(q.small); dfreet(q.S);
   dfree(q.W); dfree(q.Zo); dfree(q.W2); dfree(q.Z2); dfreet(q.jw); dfreet(q.S2);
+  dfreet(q.Vs); dfreet(q.Ps); dfreet(q.ws);
   q.ncv = 0;
 }
 
@@ -332,7 +335,8 @@ struct Driver {
 
   void cgs(int pass, int half = 0) {
     const int ncol = h->ncv + 1 + h->ncv;
-    launch_step_cgs<ST>(h->dprobs, h->count, h->ph, h->maxnrb, h->maxNpad, ncol, pass, half, s);
+    launch_step_cgs<ST>(h->dprobs, h->count, h->ph, h->maxnrb, h->maxNpad, ncol, pass, half, h->mixed && h->ph,
+                        s);
   }
 
   void normalize(int start, int half, cudaStream_t st) {
@@ -706,6 +710,11 @@ int alloc_solve(bse_handle* h, int ncv) {
     if ((rc = dalloc(&q.part, cs * (size_t)q.nT * q.nT * TS))) return rc;
     if (h->mixed) {
       if ((rc = dalloc(&q.xs, sizeof(float4) * (size_t)q.Npad))) return rc;
+      if ((rc = dalloc((void**)&q.Vs, sizeof(float4) * (size_t)q.Npad * nbas))) return rc;
+      if ((rc = dalloc((void**)&q.Ps, sizeof(float4) * (size_t)q.Npad * nbas))) return rc;
+      if ((rc = dalloc((void**)&q.ws, sizeof(float4) * (size_t)q.Npad))) return rc;
+      CK(cudaMemsetAsync(q.Vs, 0, sizeof(float4) * (size_t)q.Npad * nbas, h->stream));
+      CK(cudaMemsetAsync(q.Ps, 0, sizeof(float4) * (size_t)q.Npad * nbas, h->stream));
       if ((rc = dalloc((void**)&q.xmax, sizeof(float) * (size_t)q.nT))) return rc;
     }
     if ((rc = dalloc((void**)&q.cpart, sizeof(double2) * (size_t)nrb * ncol))) return rc;
@@ -788,6 +797,7 @@ int upload_probs(bse_handle* h) {
     d.jw = q.jw;
     d.jwld = 2 * q.ncv + 2;
     d.S2 = q.S2;
+    d.Vs = q.Vs; d.Ps = q.Ps; d.ws = q.ws;
   }
   CK(cudaMemcpyAsync(h->dprobs, h->hprobs.data(), sizeof(Prob) * h->count, cudaMemcpyHostToDevice,
                      h->stream));

@@ -58,6 +58,12 @@ template <typename T, typename R> __host__ __device__ inline T cscale(T a, R s) 
 
 struct alignas(32) D4 { double x, y, z, w; };
 
+// FP64 complex -> {re_hi, im_hi, re_lo, im_lo}: hi = fl32(v), lo = fl32(v - hi) (48 bits of v)
+__host__ __device__ inline float4 dsplit(double2 v) {
+  const float xh = (float)v.x, yh = (float)v.y;
+  return make_float4(xh, yh, (float)(v.x - (double)xh), (float)(v.y - (double)yh));
+}
+
 template <typename To, typename From> __host__ __device__ inline To ccvt(From a) {
   To r; r.x = a.x; r.y = a.y; return r;
 }
@@ -147,6 +153,12 @@ struct Prob {
   double* jw;
   int jwld;           // 2 ncv + 2
   double* S2;
+  // mixed PH path: double-FP32 shadows {re_hi, im_hi, re_lo, im_lo} of the FP64 basis V, P
+  // (Npad x (ncv + 1)) and of the work vector w, kept in step with them, so that the
+  // Gram-Schmidt passes run on the FP32 pipes (null elsewhere)
+  float4* Vs;
+  float4* Ps;
+  float4* ws;
 };
 
 // Jobs of the tiled product: problem, tile row I, tile column J, tile index.
@@ -291,7 +303,7 @@ int dense_shao(const Prob* dprobs, int64_t N, int64_t Npad, bool tiles64, bool p
 // and the twins i V), 2 its even half and its fresh vectors (against V and the twins i W)
 template <typename ST>
 void launch_step_cgs(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t maxNpad,
-                     int ncol, int pass, int half, cudaStream_t s);
+                     int ncol, int pass, int half, bool dfs, cudaStream_t s);
 template <typename ST>
 void launch_step_normalize(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t maxNpad,
                            int start, int half, cudaStream_t s);

@@ -566,6 +566,18 @@ __device__ __forceinline__ void norm_dest(const Prob& p, const KState* st, int h
   }
 }
 
+// The double-FP32 shadows of a new V (and P) column, where the problem keeps them.
+template <typename ST>
+__device__ __forceinline__ void shadow_store(const Prob& p, const KState* st, int half, int64_t row, ST xv, ST yv) {
+  if constexpr (std::is_same<ST, double2>::value) {
+    if (p.Vs && half != 1) {
+      const int64_t o = (int64_t)(st->j + 1) * p.Npad + row;
+      p.Vs[o] = dsplit(xv);
+      if (p.ph) p.Ps[o] = dsplit(yv);
+    }
+  }
+}
+
 // X = w / beta, Y = pw / beta (norm_dest) when beta^2 is usable.
 // One unit: rows bx * blockDim.x ... of problem ip; sb2: one double of shared memory.
 template <typename ST, bool COH = false>
@@ -585,8 +597,11 @@ __device__ __forceinline__ void normalize_body(const Prob* __restrict__ probs, i
   if (row >= p.Npad) return;
   ST *X, *Y;
   norm_dest<ST>(p, st, half, X, Y);
-  X[row] = cscale(ldp<COH>((const ST*)p.w + row), inv);
-  if (ph) Y[row] = cscale(ldp<COH>((const ST*)p.pw + row), inv);
+  const ST xv = cscale(ldp<COH>((const ST*)p.w + row), inv);
+  X[row] = xv;
+  ST yv = czero<ST>();
+  if (ph) Y[row] = yv = cscale(ldp<COH>((const ST*)p.pw + row), inv);
+  shadow_store<ST>(p, st, half, row, xv, yv);
 }
 
 // Record alpha_j, beta_j, advance j, given beta^2 = b2 of the new vector.  fresh = 0:
@@ -703,8 +718,11 @@ __device__ __forceinline__ void norm_fused_body(const Prob* __restrict__ probs, 
     ST *X, *Y;
     norm_dest<ST>(p, st, half, X, Y);
     for (int64_t r = threadIdx.x; r < p.Npad; r += 256) {
-      X[r] = cscale(ldp<COH>(w + r), inv);
-      if (ph) Y[r] = cscale(ldp<COH>((const ST*)p.pw + r), inv);
+      const ST xv = cscale(ldp<COH>(w + r), inv);
+      X[r] = xv;
+      ST yv = czero<ST>();
+      if (ph) Y[r] = yv = cscale(ldp<COH>((const ST*)p.pw + r), inv);
+      shadow_store<ST>(p, st, half, r, xv, yv);
     }
   }
   __syncthreads();                     // every thread has read st->j

@@ -66,6 +66,167 @@ k_cgs_update(const Prob* __restrict__ probs, int ph, int pass, int newvec, int h
   cgs_update_body<ST, false>(probs, ph, pass, newvec, half, blockIdx.x, blockIdx.y, cf, red);
 }
 
+// ---------------------------------------------------------------- double-FP32 Gram-Schmidt
+// The folded step's CGS passes on the mixed path, on the double-FP32 shadows of V, P and w
+// (48 bits of each FP64 value): a product a b of two (hi, lo) numbers is hi*hi exactly (its FMA
+// residual) plus the two cross terms, sums are (hi, lo) pairs kept with Knuth's TwoSum, about
+// 2^-44 relative per term.  GB300 runs FP64 at 1/64 of the FP32 rate, and the FP64 passes were
+// bound by it, not by HBM; here the FP32 pipes carry them.  Same units, same partial-sum slots
+// and the same fixed summation orders as k_cgs_dot / k_cgs_update.
+__device__ __forceinline__ void df_madd(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  const float pr = ah * bh;
+  const float e = __fmaf_rn(ah, bh, -pr);
+  const float t = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
+  const float su = sh + pr;
+  const float bb = su - sh;
+  const float err = (sh - (su - bb)) + (pr - bb);
+  sh = su;
+  sl += err + t;
+}
+__device__ __forceinline__ void df_add(float& sh, float& sl, float bh, float bl) {
+  const float su = sh + bh;
+  const float bb = su - sh;
+  const float err = (sh - (su - bb)) + (bh - bb);
+  sh = su;
+  sl += err + bl;
+}
+
+// units and output as k_cgs_dot (folded step, half 0: Re(P^H w) and Im(V^H w))
+__global__ void __launch_bounds__(256)
+k_cgs_dot_dfs(const Prob* __restrict__ probs, int newvec) {
+  __shared__ double red[2][4];
+  const Prob& p = probs[blockIdx.z];
+  const KState* st = p.st;
+  if (!kphase(st, newvec)) return;
+  const int rb = blockIdx.y;
+  if (rb >= p.nrb) return;
+  const int j = st->j;
+  const int nset = 2 * (j + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int hw = warp >> 2, quarter = warp & 3;
+  const int c = blockIdx.x * 2 + hw;
+  if (blockIdx.x * 2 >= nset) return;                     // whole CTA
+  double a = 0.0;
+  if (c < nset) {
+    const bool twin = c > j;                              // warp-uniform
+    const int col = twin ? c - (j + 1) : c;
+    const float4* Q = (twin ? p.Vs : p.Ps) + (int64_t)col * p.Npad;
+    const float4* w = p.ws;
+    const int64_t r0 = (int64_t)rb * ROWBLK + quarter * (ROWBLK / 4);
+    const int64_t r1 = min((int64_t)p.Npad, r0 + ROWBLK / 4);
+    float sh = 0.f, sl = 0.f;
+    int64_t r = r0 + lane;
+    for (; r + 3 * 32 < r1; r += 4 * 32) {
+      float4 q[4], x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        q[u] = __ldg(Q + r + 32 * u);
+        x[u] = __ldg(w + r + 32 * u);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (twin) {              // Im(conj(q) x) = q_re x_im - q_im x_re
+          df_madd(sh, sl, q[u].x, q[u].z, x[u].y, x[u].w);
+          df_madd(sh, sl, -q[u].y, -q[u].w, x[u].x, x[u].z);
+        } else {                 // Re(conj(q) x) = q_re x_re + q_im x_im
+          df_madd(sh, sl, q[u].x, q[u].z, x[u].x, x[u].z);
+          df_madd(sh, sl, q[u].y, q[u].w, x[u].y, x[u].w);
+        }
+      }
+    }
+    for (; r < r1; r += 32) {
+      const float4 q = __ldg(Q + r), x = __ldg(w + r);
+      if (twin) {
+        df_madd(sh, sl, q.x, q.z, x.y, x.w);
+        df_madd(sh, sl, -q.y, -q.w, x.x, x.z);
+      } else {
+        df_madd(sh, sl, q.x, q.z, x.x, x.z);
+        df_madd(sh, sl, q.y, q.w, x.y, x.w);
+      }
+    }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, sh, m), ol = __shfl_xor_sync(0xffffffffu, sl, m);
+      df_add(sh, sl, oh, ol);
+    }
+    a = (double)sh + (double)sl;
+  }
+  if (lane == 0) red[hw][quarter] = a;
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    const int cc = blockIdx.x * 2 + threadIdx.x;
+    if (cc < nset) {
+      double t = red[threadIdx.x][0];
+#pragma unroll
+      for (int q = 1; q < 4; ++q) t += red[threadIdx.x][q];
+      ((double2*)p.cpart)[(int64_t)rb * p.ncol + cc] = mk(t, 0.0);
+    }
+  }
+}
+
+// units as k_cgs_update: w = w - V c - i P d (c, d the pass's real coefficients), and ws
+__global__ void __launch_bounds__(256, 3)
+k_cgs_update_dfs(const Prob* __restrict__ probs, int pass, int newvec) {
+  __shared__ float2 cf[2 * MAXM + 2];
+  __shared__ float4 red[8][32];
+  const Prob& p = probs[blockIdx.y];
+  const KState* st = p.st;
+  if (!kphase(st, newvec)) return;
+  const int64_t row = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
+  if ((int64_t)blockIdx.x * 32 >= p.Npad) return;     // whole block (Npad is a multiple of 128)
+  const int nj = st->j + 1;
+  const int nset = 2 * nj;
+  const double2* cp = (const double2*)p.cpart;
+  double2* coef = (double2*)p.coef + (int64_t)(pass & 1) * p.ncol;
+  for (int c = threadIdx.x; c < nset; c += blockDim.x) {
+    double sc = 0.0;
+    int rb = 0;
+    for (; rb + 8 <= p.nrb; rb += 8) {      // eight loads in flight, then the sums in order
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = cp[(int64_t)(rb + u) * p.ncol + c].x;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) sc += v[u];
+    }
+    for (; rb < p.nrb; ++rb) sc += cp[(int64_t)rb * p.ncol + c].x;
+    const float h = (float)sc;
+    cf[c] = make_float2(h, (float)(sc - (double)h));
+    if (blockIdx.x == 0) coef[c] = mk(sc, 0.0);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // entry cc: V[:, cc] (cc < nj) or the twin i P[:, cc - nj] = (-P_im, P_re)
+  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+  for (int c = warp; c < nset; c += 8) {
+    const bool tw = c >= nj;
+    const float4 v = __ldg((tw ? p.Ps : p.Vs) + (int64_t)(tw ? c - nj : c) * p.Npad + row);
+    const float2 f = cf[c];
+    if (tw) {
+      df_madd(rh, rl, -v.y, -v.w, f.x, f.y);
+      df_madd(ih, il, v.x, v.z, f.x, f.y);
+    } else {
+      df_madd(rh, rl, v.x, v.z, f.x, f.y);
+      df_madd(ih, il, v.y, v.w, f.x, f.y);
+    }
+  }
+  red[warp][lane] = make_float4(rh, rl, ih, il);
+  __syncthreads();
+  if (warp == 0) {
+    float4 t = red[0][lane];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) {
+      const float4 o = red[q][lane];
+      df_add(t.x, t.y, o.x, o.y);
+      df_add(t.z, t.w, o.z, o.w);
+    }
+    double2* w = (double2*)p.w;
+    const double2 x = w[row];
+    const double2 y = mk(x.x - ((double)t.x + (double)t.y), x.y - ((double)t.z + (double)t.w));
+    w[row] = y;
+    p.ws[row] = dsplit(y);
+  }
+}
+
 template <typename ST>
 __global__ void __launch_bounds__(256)
 k_norm_partial(const Prob* __restrict__ probs, int ph, int start) {
@@ -132,6 +293,8 @@ __global__ void k_start_fill(const Prob* __restrict__ probs, uint64_t seed, cons
     else v = ccvt<ST>(hash_normal(seed + 0x51ed27ull * (uint64_t)(blockIdx.y + 1) + (uint64_t)st->restarts, row));
   }
   ((ST*)p.w)[row] = v;
+  if constexpr (std::is_same<ST, double2>::value)
+    if (p.ws) p.ws[row] = dsplit(v);
 }
 
 // ---------------------------------------------------------------- restart
@@ -295,6 +458,18 @@ __global__ void k_restart_copy(const Prob* __restrict__ probs, int ph, int gk) {
     for (int i = 0; i < nkeep; ++i) P[(int64_t)(k0 + i) * p.Npad + row] = P2[(int64_t)i * p.Npad + row];
     P[(int64_t)(k0 + nkeep) * p.Npad + row] = pm;
   }
+  if constexpr (std::is_same<ST, double2>::value) {
+    if (p.Vs) {                         // the double-FP32 shadows follow
+      for (int i = 0; i < nkeep; ++i)
+        p.Vs[(int64_t)(k0 + i) * p.Npad + row] = dsplit(((const double2*)p.V2)[(int64_t)i * p.Npad + row]);
+      p.Vs[(int64_t)(k0 + nkeep) * p.Npad + row] = dsplit(vm);
+      if (ph) {
+        for (int i = 0; i < nkeep; ++i)
+          p.Ps[(int64_t)(k0 + i) * p.Npad + row] = dsplit(((const double2*)p.P2)[(int64_t)i * p.Npad + row]);
+        p.Ps[(int64_t)(k0 + nkeep) * p.Npad + row] = dsplit(((const double2*)p.P)[(int64_t)(k0 + nkeep) * p.Npad + row]);
+      }
+    }
+  }
   if (gk) {
     ST* W = (ST*)p.W;
     ST* Z = (ST*)p.Z;
@@ -329,11 +504,16 @@ __global__ void k_restart_commit(const Prob* __restrict__ probs, int nprob, int 
 // ---------------------------------------------------------------- launchers
 template <typename ST>
 void launch_step_cgs(const Prob* dprobs, int nprob, int ph, int maxnrb, int64_t maxNpad, int ncol,
-                     int pass, int half, cudaStream_t s) {
+                     int pass, int half, bool dfs, cudaStream_t s) {
   // pass: 0/1 regular step passes; 2/3 the same for a fresh (replacement) vector
   count_launch(2);
   const int newvec = pass >= 2 ? 1 : 0;
   const int ps = pass & 1;
+  if (dfs && ph && half == 0) {        // the double-FP32 shadows of the mixed path
+    k_cgs_dot_dfs<<<dim3((ncol + 1) / 2, maxnrb, nprob), 256, 0, s>>>(dprobs, newvec);
+    k_cgs_update_dfs<<<dim3((unsigned)((maxNpad + 31) / 32), nprob), 256, 0, s>>>(dprobs, ps, newvec);
+    return;
+  }
   k_cgs_dot<ST><<<dim3((ncol + 1) / 2, maxnrb, nprob), 256, 0, s>>>(dprobs, ph, newvec, half, ps);
   k_cgs_update<ST><<<dim3((unsigned)((maxNpad + 31) / 32), nprob), 256, 0, s>>>(dprobs, ph, ps, newvec, half);
 }
@@ -380,7 +560,7 @@ void launch_restart(const Prob* dprobs, int nprob, int ph, int64_t maxNpad, int 
 }
 
 #define INST(ST)                                                                                        \
-  template void launch_step_cgs<ST>(const Prob*, int, int, int, int64_t, int, int, int, cudaStream_t); \
+  template void launch_step_cgs<ST>(const Prob*, int, int, int, int64_t, int, int, int, bool, cudaStream_t); \
   template void launch_step_normalize<ST>(const Prob*, int, int, int, int64_t, int, int, cudaStream_t); \
   template void launch_start_vector<ST>(const Prob*, int, int64_t, uint64_t, const void*,              \
                                         cudaStream_t);                                                  \

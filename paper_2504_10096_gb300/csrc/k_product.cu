@@ -82,6 +82,7 @@ k_prod_reduce_dfc(const Prob* __restrict__ probs, int mode, GenericIO io) {
 #pragma unroll
     for (int q = 0; q < REDUCE_GROUPS - 1; ++q) acc = cadd(acc, grp[q][r]);
     y[(int64_t)I * TS + r] = acc;
+    if (p.ws && y == (double2*)p.w) p.ws[(int64_t)I * TS + r] = dsplit(acc);   // its double-FP32 shadow
   }
 }
 

@@ -67,9 +67,11 @@ typedef enum bse_dtype {
   /* complex64 input and storage of A and B (half the bytes of BSE_C128);
      FP64 Krylov basis; the Lanczos products in double-FP32 arithmetic on
      the complex64 tiles (each stored value is exact in FP32), so the
-     folded iteration is not limited by FP32 rounding; FP64 projected
-     problem, residuals and Rayleigh quotients.  Eigenvectors are returned
-     as complex64. */
+     folded iteration is not limited by FP32 rounding -- the small tiles
+     (tile_tau) with rounded A + B, A - B and fixed-point-grid sums; the
+     Gram-Schmidt passes and the restart in double-FP32 on FP32 shadows of
+     the basis (about 2^-44 relative); FP64 projected problem, residuals and
+     Rayleigh quotients.  Eigenvectors are returned as complex64. */
   BSE_C64_MIXED = 2,
   /* complex128 input and storage, FP64 Krylov basis, projected problem and
      final residuals; the streaming Lanczos products in double-FP32

@@ -276,8 +276,8 @@ def run_gpu(args):
     adj_ms = a0.elapsed_time(a1)
     del dA, dB
     s.close()
-    Ah = A.cpu().numpy()
-    Bh = B.cpu().numpy()
+    Ah = A.cpu().pin_memory().numpy()                        # pinned host buffers (DMA copies)
+    Bh = B.cpu().pin_memory().numpy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_steps = max(1, min(2, args.steps))
